@@ -1,0 +1,503 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and the mathematics.
+
+Nothing here retypes the oracle's formulas: each check is a closed form, an
+exact invariant, a brute-force enumeration or an independent definition, chosen
+so that a dropped term, a wrong sign or a transposed operand in the oracle
+fails at least one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+from paper_2605_28525_b300 import workloads as W
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")))
+
+
+def make(oracle_mod, **kw):
+    base = dict(lo=(0, 0, 0), hi=(32, 32, 32), h=1.0 / 32, dt=1e-4, g=(0.0, 0.0, -9.81), B=4,
+                material=oracle_mod.NEOHOOKEAN, E=1e5, nu=0.3, rho=1000.0, ppc=8.0)
+    base.update(kw)
+    return oracle_mod.Oracle(**base)
+
+
+# ---------------------------------------------------------------- B-spline
+
+def _bspline_by_convolution(t):
+    """Quadratic B-spline as the unit box convolved with the linear hat:
+    N2(t) = int_{t-1/2}^{t+1/2} max(0, 1-|s|) ds (independent definition)."""
+    hat = lambda s: max(0.0, 1.0 - abs(s))
+    val, _ = integrate.quad(hat, t - 0.5, t + 0.5, points=[-1.0, 0.0, 1.0], epsabs=1e-14, epsrel=1e-14)
+    return val
+
+
+@pytest.mark.parametrize("xh", [(10.3, 11.7, 12.5), (10.5, 10.0, 9.9999), (4.75, 20.25, 7.125)])
+def test_weights_match_box_hat_convolution(oracle_mod, xh):
+    o = make(oracle_mod)
+    x = np.array(xh) * o.p.h
+    nodes, w, gw = o.weights(x)
+    for q in range(27):
+        t = np.array(xh) - nodes[q]
+        ref = np.prod([_bspline_by_convolution(t[a]) for a in range(3)])
+        assert abs(w[q] - ref) < 1e-12
+
+
+def test_weights_partition_linear_gradient_identities(oracle_mod):
+    o = make(oracle_mod)
+    rng = np.random.default_rng(0)
+    h = o.p.h
+    for _ in range(200):
+        x = (8 + 16 * rng.random(3)) * h
+        nodes, w, gw = o.weights(x)
+        xn = nodes * h
+        assert abs(w.sum() - 1.0) < 1e-14                                   # partition of unity
+        assert np.allclose((w[:, None] * xn).sum(0), x, atol=1e-14)         # linear reproduction
+        assert np.allclose(gw.sum(0), 0.0, atol=1e-11)                      # sum grad N = 0
+        assert np.allclose(np.einsum("qi,qj->ij", xn, gw), np.eye(3), atol=1e-12)  # grad of x = I
+        assert np.allclose(o.Dp(x), np.eye(3) * h * h / 4.0, atol=1e-16)    # APIC D_p closed form
+        # stencil: all 27 nodes, base = floor(x/h - 1/2)
+        assert np.array_equal(nodes.min(0), np.floor(x / h - 0.5).astype(int))
+        assert np.array_equal(nodes.max(0) - nodes.min(0), [2, 2, 2])
+
+
+def test_gradient_is_derivative_of_weight(oracle_mod):
+    o = make(oracle_mod)
+    rng = np.random.default_rng(1)
+    h = o.p.h
+    for _ in range(20):
+        x = (8.1 + 15 * rng.random(3)) * h
+        nodes, w, gw = o.weights(x)
+        for a in range(3):
+            e = np.zeros(3)
+            e[a] = 1e-7 * h
+            # keep the same stencil for the difference
+            n2, wp, _ = o.weights(x + e)
+            n3, wm, _ = o.weights(x - e)
+            if not (np.array_equal(n2, nodes) and np.array_equal(n3, nodes)):
+                continue
+            fd = (wp - wm) / (2e-7 * h)
+            assert np.allclose(fd, gw[:, a], atol=1e-5 / h)
+
+
+# ----------------------------------------------------------- active set
+
+def _eq_key(b, m=GOLDEN["key_bits_m"]["value"], bias=GOLDEN["key_bias_b"]["value"]):
+    return ((b[0] + bias) << (2 * m)) | ((b[1] + bias) << m) | (b[2] + bias)
+
+
+def _brute_force_blocks(x, h, B):
+    blocks = set()
+    for p in x.astype(np.float64):
+        base = np.floor(p / h - 0.5).astype(int)
+        for a in range(3):
+            for b in range(3):
+                for c in range(3):
+                    n = base + (a, b, c)
+                    blocks.add(tuple(int(v) // B for v in n))   # python // is floor division
+    return sorted(blocks, key=_eq_key)
+
+
+@pytest.mark.parametrize("B", [1, 4])
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_active_blocks_equal_brute_force(oracle_mod, B, seed):
+    o = make(oracle_mod, B=B)
+    rng = np.random.default_rng(seed)
+    n = 300
+    x = ((4 + 24 * rng.random((n, 3))) * o.p.h).astype(np.float32)
+    got = o.active_blocks(x)
+    want = np.array(_brute_force_blocks(x, o.p.h, B), dtype=np.int32)
+    assert np.array_equal(got, want)
+
+
+def test_active_blocks_negative_indices_use_floor(oracle_mod):
+    o = make(oracle_mod, lo=(-40, -40, -40), hi=(8, 8, 8), B=4)
+    x = np.array([[-5.3, -0.2, -9.9], [-1.1, -1.5, 1.2]]) * o.p.h
+    got = o.active_blocks(x.astype(np.float32))
+    want = np.array(_brute_force_blocks(x.astype(np.float32), o.p.h, 4), dtype=np.int32)
+    assert np.array_equal(got, want)
+
+
+def test_active_blocks_hand_cases(oracle_mod):
+    o = make(oracle_mod, B=4)
+    h = o.p.h
+    # stencil nodes 9..11 on every axis -> block 2 only
+    assert np.array_equal(o.active_blocks(np.array([[10.3, 10.3, 10.3]]) * h), [[2, 2, 2]])
+    # stencil nodes 11..13 cross into block 3 on every axis -> 8 blocks in key order
+    got = o.active_blocks(np.array([[11.7, 11.7, 11.7]]) * h)
+    want = [[i, j, k] for i in (2, 3) for j in (2, 3) for k in (2, 3)]
+    assert np.array_equal(got, want)
+    # B = 1: the 27 stencil nodes themselves, i-major k-fastest
+    o1 = make(oracle_mod, B=1)
+    got = o1.active_blocks(np.array([[10.3, 10.3, 10.3]]) * h)
+    want = [[i, j, k] for i in (9, 10, 11) for j in (9, 10, 11) for k in (9, 10, 11)]
+    assert np.array_equal(got, want)
+
+
+def test_key_order_is_i_major(oracle_mod):
+    lo, hi = GOLDEN["key_index_range"]["value"]
+    assert _eq_key((lo, lo, lo)) == 0
+    assert _eq_key((hi, hi, hi)) == (1 << 63) - 1
+    assert _eq_key((0, 0, 1)) - _eq_key((0, 0, 0)) == 1
+    assert _eq_key((1, 0, 0)) > _eq_key((0, hi, hi))
+
+
+# ------------------------------------------------------------------- P2G
+
+def _random_state(n, seed, lo=8, hi=24, h=1.0 / 32):
+    return W.random_state(n, (lo,) * 3, (hi,) * 3, h, seed=seed)
+
+
+@pytest.mark.parametrize("material", [0, 1])
+def test_p2g_conservation(oracle_mod, material):
+    o = make(oracle_mod, material=material, phi_deg=30.0)
+    x, v, Cm, F = _random_state(500, 4)
+    m, mv, f = o.p2g(x, v, Cm, F)
+    h = o.p.h
+    mp = o.p.rho * h ** 3 / o.p.ppc
+    xn = o.dense_nodes() * h
+    x64 = x.astype(np.float64)
+    v64, C64 = v.astype(np.float64), Cm.astype(np.float64)
+    assert abs(m.sum() - mp * len(x)) < 1e-12 * mp * len(x)                      # mass
+    assert np.allclose(mv.sum(0), mp * v64.sum(0), rtol=0, atol=1e-12 * mp * len(x))  # linear momentum
+    assert np.allclose((m[:, None] * xn).sum(0), mp * x64.sum(0), atol=1e-12)    # centre of mass
+    # APIC angular momentum: sum x_n x (mv)_n = sum m_p [x_p x v_p + (h^2/4) eps_ijk C_kj]
+    L_grid = np.cross(xn, mv).sum(0)
+    eps = np.zeros((3, 3, 3))
+    eps[0, 1, 2] = eps[1, 2, 0] = eps[2, 0, 1] = 1
+    eps[0, 2, 1] = eps[2, 1, 0] = eps[1, 0, 2] = -1
+    L_part = mp * (np.cross(x64, v64).sum(0) + (h * h / 4) * np.einsum("ijk,pkj->i", eps, C64))
+    assert np.allclose(L_grid, L_part, atol=1e-12)
+    # internal forces: zero net force and zero net torque (sigma symmetric)
+    scale = np.abs(f).sum()
+    assert np.allclose(f.sum(0), 0.0, atol=1e-12 * scale)
+    assert np.allclose(np.cross(xn, f).sum(0), 0.0, atol=1e-12 * scale)
+    # stress virial: sum_n f_n x_n^T = -sum_p V0 tau_p  (because sum_n x_n grad N^T = I)
+    V0 = h ** 3 / o.p.ppc
+    tau_sum = sum(o.kirchhoff(F[p]) for p in range(len(x))) * V0
+    assert np.allclose(np.einsum("ni,nj->ij", f, xn), -tau_sum, atol=1e-10 * np.abs(tau_sum).max())
+
+
+def test_p2g_nodes_equals_dense(oracle_mod):
+    o = make(oracle_mod, material=1)
+    x, v, Cm, F = _random_state(200, 5)
+    m, mv, f = o.p2g(x, v, Cm, F)
+    idx = np.flatnonzero(m)[::37]
+    nodes = o.dense_nodes()[idx]
+    m2, mv2, f2 = o.p2g_nodes(nodes, x, v, Cm, F)
+    assert np.allclose(m2, m[idx], rtol=1e-14)
+    assert np.allclose(mv2, mv[idx], rtol=1e-13, atol=1e-18)
+    assert np.allclose(f2, f[idx], rtol=1e-12, atol=1e-14)
+
+
+def test_p2g_no_mass_outside_active_blocks(oracle_mod):
+    """Dense P2G touches only nodes of the active block set (sparse == dense support)."""
+    o = make(oracle_mod, B=4)
+    x, v, Cm, F = _random_state(100, 6)
+    m, _, _ = o.p2g(x, v, Cm, F)
+    blocks = set(map(tuple, o.active_blocks(x)))
+    nodes = o.dense_nodes()[m > 0]
+    assert all(tuple(int(c) // 4 for c in n) in blocks for n in nodes)
+
+
+# ------------------------------------------------------- full-step pins
+
+def _blob(oracle_mod, n=400, seed=7):
+    x, _, _, _ = _random_state(n, seed, lo=12, hi=20)
+    return x
+
+
+def test_free_fall_closed_form(oracle_mod):
+    o = make(oracle_mod, E=1e5, wall_layers=2)
+    x0 = _blob(oracle_mod).astype(np.float64)
+    g, dt = 9.81, o.p.dt
+    for n in (1, 5, 20):
+        x, v, Cm, F = o.run(x0, nsteps=n)
+        assert np.allclose(x[:, 2], x0[:, 2] - g * dt * dt * n * (n + 1) / 2, atol=1e-13)
+        assert np.allclose(x[:, :2], x0[:, :2], atol=1e-15)
+        assert np.allclose(v, [0, 0, -g * dt * n], atol=1e-13)
+        assert np.allclose(Cm, 0, atol=1e-9)
+        assert np.allclose(F, np.eye(3), atol=1e-13)
+
+
+def test_rigid_translation(oracle_mod):
+    o = make(oracle_mod, g=(0, 0, 0))
+    x0 = _blob(oracle_mod).astype(np.float64)
+    v0 = np.array([0.3, -0.2, 0.1])
+    n = 10
+    x, v, Cm, F = o.run(x0, np.broadcast_to(v0, x0.shape), nsteps=n)
+    assert np.allclose(x, x0 + n * o.p.dt * v0, atol=1e-14)
+    assert np.allclose(v, v0, atol=1e-13)
+    assert np.allclose(Cm, 0, atol=1e-9)
+    assert np.allclose(F, np.eye(3), atol=1e-13)
+
+
+def test_affine_field_reproduced(oracle_mod):
+    """APIC reproduces an affine velocity field exactly (Jiang et al. 2015)."""
+    o = make(oracle_mod, g=(0, 0, 0), E=0.0)
+    x0 = _blob(oracle_mod).astype(np.float64)
+    A = np.array([[0.5, -1.0, 0.2], [0.3, 0.1, -0.4], [-0.6, 0.7, 0.25]])
+    v0 = np.array([0.1, 0.2, -0.3])
+    vp = v0 + x0 @ A.T
+    Cp = np.broadcast_to(A, (len(x0), 3, 3))
+    F0 = np.array([[1.1, 0.2, 0.0], [-0.1, 0.9, 0.3], [0.05, 0.0, 1.2]])
+    x, v, Cm, F = o.run(x0, vp, Cp, np.broadcast_to(F0, (len(x0), 3, 3)), nsteps=1)
+    assert np.allclose(v, vp, atol=1e-13)
+    assert np.allclose(Cm, A, atol=1e-10)
+    assert np.allclose(x, x0 + o.p.dt * vp, atol=1e-15)
+    assert np.allclose(F, (np.eye(3) + o.p.dt * A) @ F0, atol=1e-13)   # F <- (I + dt grad v) F
+
+
+def test_grid_update_limits(oracle_mod):
+    o = make(oracle_mod, floor_kind=oracle_mod.FLOOR_STICKY, floor_z=5 / 32, wall_layers=2)
+    mv, f = np.array([0.3, 0.2, -0.5]), np.array([1.0, 2.0, 3.0])
+    # interior node: v = mv/m + dt (f/m + g)
+    v = o.grid_node((10, 10, 10), 2.0, mv, f)
+    assert np.allclose(v, mv / 2 + o.p.dt * (f / 2 + np.array([0, 0, -9.81])), atol=1e-15)
+    assert np.array_equal(o.grid_node((10, 10, 10), 0.0, mv, f), [0, 0, 0])       # m = 0
+    assert np.array_equal(o.grid_node((10, 10, 5), 2.0, mv, f), [0, 0, 0])        # sticky floor
+    assert np.array_equal(o.grid_node((1, 10, 10), 2.0, mv, f), [0, 0, 0])        # wall
+    assert np.array_equal(o.grid_node((10, 31, 10), 2.0, mv, f), [0, 0, 0])       # wall (hi side)
+    slip = make(oracle_mod, floor_kind=oracle_mod.FLOOR_SLIP, floor_z=5 / 32, g=(0, 0, 0), dt=0.0)
+    assert np.allclose(slip.grid_node((10, 10, 4), 1.0, [0.3, 0.2, -0.5], [0, 0, 0]), [0.3, 0.2, 0.0])
+    assert np.allclose(slip.grid_node((10, 10, 4), 1.0, [0.3, 0.2, 0.5], [0, 0, 0]), [0.3, 0.2, 0.5])
+    cou = make(oracle_mod, floor_kind=oracle_mod.FLOOR_COULOMB, floor_z=5 / 32, floor_mu=0.5, g=(0, 0, 0),
+               dt=0.0)
+    # approaching: tangential speed 0.5 reduced by mu |vn| = 0.1 -> 0.4
+    assert np.allclose(cou.grid_node((10, 10, 4), 1.0, [0.3, 0.4, -0.2], [0, 0, 0]), [0.24, 0.32, 0.0])
+    # friction exceeds tangential speed -> stop
+    assert np.allclose(cou.grid_node((10, 10, 4), 1.0, [0.03, 0.04, -0.2], [0, 0, 0]), [0, 0, 0])
+    # separating: unchanged
+    assert np.allclose(cou.grid_node((10, 10, 4), 1.0, [0.3, 0.4, 0.2], [0, 0, 0]), [0.3, 0.4, 0.2])
+
+
+def test_terrain_flat_equals_floor(oracle_mod):
+    """A flat level-set terrain at height z0 acts as a Coulomb floor at z0."""
+    t = np.full((33, 33), 5 / 32)
+    ter = make(oracle_mod, terrain=t, terrain_mu=0.5, g=(0, 0, 0), dt=0.0)
+    flo = make(oracle_mod, floor_kind=oracle_mod.FLOOR_COULOMB, floor_z=5 / 32, floor_mu=0.5, g=(0, 0, 0),
+               dt=0.0)
+    rng = np.random.default_rng(3)
+    for _ in range(50):
+        n = rng.integers(3, 29, size=3)
+        mv = rng.standard_normal(3)
+        assert np.allclose(ter.grid_node(n, 1.0, mv, [0, 0, 0]), flo.grid_node(n, 1.0, mv, [0, 0, 0]))
+
+
+def test_terrain_tilted_plane_normal(oracle_mod):
+    """On a plane z = s x the terrain normal is (-s, 0, 1)/|.|: a velocity along
+    the plane is untouched, one into the plane loses its normal part."""
+    h = 1.0 / 32
+    s = 0.3
+    xs = np.arange(33) * h
+    t = np.broadcast_to(5 * h + s * xs, (33, 33)).copy()
+    ter = make(oracle_mod, terrain=t, terrain_mu=0.0, g=(0, 0, 0), dt=0.0)
+    nrm = np.array([-s, 0, 1]) / math.hypot(s, 1)
+    along = np.array([1.0, 0.0, s])
+    assert np.allclose(ter.grid_node((10, 10, 4), 1.0, along, [0, 0, 0]), along)
+    into = along - 2.0 * nrm
+    assert np.allclose(ter.grid_node((10, 10, 4), 1.0, into, [0, 0, 0]), along, atol=1e-12)
+
+
+# ------------------------------------------------------- constitutive pins
+
+def _rot(rng):
+    q, r = np.linalg.qr(rng.standard_normal((3, 3)))
+    q = q * np.sign(np.diag(r))
+    if np.linalg.det(q) < 0:
+        q[:, 0] = -q[:, 0]
+    return q
+
+
+@pytest.mark.parametrize("material", [0, 1])
+def test_stress_zero_for_rigid_motion_and_linear_limit(oracle_mod, material):
+    o = make(oracle_mod, material=material, E=1e7, nu=0.3)
+    mu = o.p.E / (2 * (1 + o.p.nu))
+    la = o.p.E * o.p.nu / ((1 + o.p.nu) * (1 - 2 * o.p.nu))
+    rng = np.random.default_rng(8)
+    assert np.allclose(o.kirchhoff(np.eye(3)), 0.0, atol=1e-9)
+    for _ in range(5):
+        R = _rot(rng)
+        assert np.allclose(o.kirchhoff(R), 0.0, atol=1e-6)
+        S = rng.standard_normal((3, 3))
+        S = 0.5 * (S + S.T)
+        e = 1e-6
+        lin = la * np.trace(e * S) * np.eye(3) + 2 * mu * e * S
+        assert np.allclose(o.kirchhoff(np.eye(3) + e * S), lin, rtol=0, atol=1e-5 * np.abs(lin).max())
+        # objectivity: tau(R F) = R tau(F) R^T
+        Fm = np.eye(3) + 0.05 * rng.standard_normal((3, 3))
+        assert np.allclose(o.kirchhoff(R @ Fm), R @ o.kirchhoff(Fm) @ R.T, atol=1e-6 * o.p.E)
+
+
+def test_svd_matches_numpy(oracle_mod):
+    rng = np.random.default_rng(9)
+    for k in range(300):
+        A = rng.standard_normal((3, 3)) if k % 3 else np.eye(3) + 0.1 * rng.standard_normal((3, 3))
+        U, S, V = oracle_mod.Oracle.svd3(A)
+        Sn = np.linalg.svd(A, compute_uv=False)
+        assert np.allclose(np.abs(S), Sn, rtol=1e-12, atol=1e-14)
+        assert np.allclose(U @ np.diag(S) @ V.T, A, atol=1e-13)
+        assert np.allclose(U.T @ U, np.eye(3), atol=1e-13) and np.allclose(V.T @ V, np.eye(3), atol=1e-13)
+        assert np.linalg.det(U) > 0 and np.linalg.det(V) > 0
+        assert np.sign(S[2]) == np.sign(np.linalg.det(A)) or abs(np.linalg.det(A)) < 1e-14
+
+
+def _hencky(F):
+    U, S, Vt = np.linalg.svd(F)
+    return np.log(S)
+
+
+def _yield(eps, phi_deg, E, nu):
+    mu = E / (2 * (1 + nu))
+    la = E * nu / ((1 + nu) * (1 - 2 * nu))
+    sp = math.sin(math.radians(phi_deg))
+    alpha = math.sqrt(2 / 3) * 2 * sp / (3 - sp)
+    tr = eps.sum()
+    return np.linalg.norm(eps - tr / 3) + (3 * la + 2 * mu) / (2 * mu) * tr * alpha
+
+
+def test_dp_return_map_invariants(oracle_mod):
+    o = make(oracle_mod, material=1, E=1e7, nu=0.3, phi_deg=30.0)
+    rng = np.random.default_rng(10)
+    seen = set()
+    for _ in range(400):
+        R1, R2 = _rot(rng), _rot(rng)
+        eps = rng.normal(-0.01, 0.02, 3)
+        F = R1 @ np.diag(np.exp(eps)) @ R2.T
+        Fo, cs = o.dp_project(F)
+        seen.add(cs)
+        eo = _hencky(Fo)
+        if eps.sum() >= 0:
+            assert cs == 1 and np.allclose(Fo.T @ Fo, np.eye(3), atol=1e-12)       # tip: Sigma = I
+        elif _yield(eps, 30.0, o.p.E, o.p.nu) <= 0:
+            assert cs == 0 and np.allclose(Fo, F, atol=1e-12)                      # inside: unchanged
+        else:
+            assert cs == 2
+            assert abs(_yield(eo, 30.0, o.p.E, o.p.nu)) < 1e-10                    # on the cone
+            assert abs(eo.sum() - eps.sum()) < 1e-12                               # volume kept
+            assert np.linalg.norm(eo - eo.mean()) < np.linalg.norm(eps - eps.mean())
+        # objectivity: project(R F) = R project(F)
+        Q = _rot(rng)
+        Fq, _ = o.dp_project(Q @ F)
+        assert np.allclose(Fq, Q @ Fo, atol=1e-11)
+    assert seen == {0, 1, 2}
+
+
+def test_dp_zero_friction_is_fully_deviatoric(oracle_mod):
+    o = make(oracle_mod, material=1, E=1e7, nu=0.3)
+    rng = np.random.default_rng(11)
+    for _ in range(50):
+        eps = rng.normal(-0.01, 0.01, 3)
+        if eps.sum() >= 0:
+            continue
+        F = _rot(rng) @ np.diag(np.exp(eps)) @ _rot(rng).T
+        Fo, cs = o.dp_project(F, phi_deg=0.0)
+        eo = _hencky(Fo)
+        assert np.allclose(eo, eps.sum() / 3, atol=1e-12)   # only the volumetric part survives
+
+
+# ------------------------------------------- Coulomb sliding block (Sec. 2.2.1)
+
+@pytest.mark.parametrize("theta", GOLDEN["sliding_box_angles_deg"]["value"])
+def test_sliding_block_coulomb_closed_form(oracle_mod, theta):
+    """Block on a Coulomb floor under gravity tilted by theta: for tan(theta) > mu
+    the displacement is s(t) = g (sin(theta) - mu cos(theta)) t^2 / 2; at 14 deg
+    (tan < mu) it must not accelerate."""
+    mu = GOLDEN["sliding_box_mu"]["value"]
+    assert abs(math.tan(math.radians(15.0)) - mu) < 5e-4
+    wl = W.sliding_block(theta, mu=math.tan(math.radians(15.0)), E=1e7, dt=6e-5, steps=2000)
+    o = oracle_mod.Oracle(lo=wl.lo, hi=wl.hi, h=wl.dx, dt=wl.dt, g=wl.gravity, B=4, material=wl.material,
+                          E=wl.E, nu=wl.nu, rho=wl.rho, ppc=wl.ppc, floor_kind=wl.floor_kind,
+                          floor_z=wl.floor_z, floor_mu=wl.floor_mu)
+    x0 = wl.x.astype(np.float64)
+    half = wl.steps // 2
+    x1, v1, C1, F1 = o.run(x0, nsteps=half)
+    x, v, Cm, F = o.run(x1, v1, C1, F1, nsteps=wl.steps - half)
+    t = wl.steps * wl.dt
+    s_num = (x[:, 0] - x0[:, 0]).mean()
+    acc = lambda th: 9.81 * (math.sin(math.radians(th)) - math.tan(math.radians(15.0)) * math.cos(math.radians(th)))
+    if theta == GOLDEN["sliding_box_sticks_deg"]["value"]:
+        assert acc(theta) < 0
+        # no acceleration between t/2 and t, and a displacement far below sliding at 20 deg
+        assert abs(v[:, 0].mean() - v1[:, 0].mean()) < 0.05 * acc(20) * t / 2
+        assert abs(s_num) < 0.15 * 0.5 * acc(20) * t * t
+    else:
+        s_ana = 0.5 * acc(theta) * t * t
+        assert abs(s_num - s_ana) < 0.06 * s_ana, (s_num, s_ana)
+        assert abs(v[:, 0].mean() - acc(theta) * t) < 0.04 * acc(theta) * t
+
+
+# ------------------------------------ stress from stored energy (independent form)
+
+def _nh_energy(F, mu, la):
+    """Compressible Neo-Hookean stored energy (Bonet and Wood)."""
+    J = np.linalg.det(F)
+    return 0.5 * mu * (np.trace(F.T @ F) - 3) - mu * math.log(J) + 0.5 * la * math.log(J) ** 2
+
+
+def _hencky_energy(F, mu, la):
+    """Quadratic energy in the logarithmic (Hencky) strain."""
+    e = np.log(np.linalg.svd(F, compute_uv=False))
+    return mu * (e @ e) + 0.5 * la * e.sum() ** 2
+
+
+@pytest.mark.parametrize("material", [0, 1])
+def test_kirchhoff_is_energy_derivative(oracle_mod, material):
+    """tau = (d psi / d F) F^T, by central differences of the stored energy."""
+    o = make(oracle_mod, material=material, E=1e6, nu=0.3)
+    mu = o.p.E / (2 * (1 + o.p.nu))
+    la = o.p.E * o.p.nu / ((1 + o.p.nu) * (1 - 2 * o.p.nu))
+    psi = _nh_energy if material == 0 else _hencky_energy
+    rng = np.random.default_rng(12)
+    for _ in range(5):
+        F = np.eye(3) + 0.2 * rng.standard_normal((3, 3))
+        if np.linalg.det(F) < 0.3:
+            continue
+        P = np.zeros((3, 3))
+        e = 1e-6
+        for i in range(3):
+            for j in range(3):
+                d = np.zeros((3, 3))
+                d[i, j] = e
+                P[i, j] = (psi(F + d, mu, la) - psi(F - d, mu, la)) / (2 * e)
+        assert np.allclose(o.kirchhoff(F), P @ F.T, rtol=0, atol=1e-5 * o.p.E)
+
+
+@pytest.mark.parametrize("phi", [20.0, 30.0, 40.0])
+def test_dp_cone_matches_mohr_coulomb_triaxial_compression(oracle_mod, phi):
+    """The cone constant alpha makes the Drucker-Prager surface pass through the
+    Mohr-Coulomb limit in triaxial compression: sigma1 = sigma2 = sigma3 (1-s)/(1+s),
+    s = sin(phi) (cohesionless, compression negative).  A state on that limit is
+    left alone; a state with a larger deviator returns onto it (the radial return
+    keeps the Lode angle, so the result is again triaxial)."""
+    o = make(oracle_mod, material=1, E=1e7, nu=0.3)
+    mu = o.p.E / (2 * (1 + o.p.nu))
+    la = o.p.E * o.p.nu / ((1 + o.p.nu) * (1 - 2 * o.p.nu))
+    sp = math.sin(math.radians(phi))
+    rng = np.random.default_rng(13)
+
+    def strain_of(stress):
+        tr_e = stress.sum() / (3 * la + 2 * mu)
+        return (stress - la * tr_e) / (2 * mu)
+
+    def stress_of(e):
+        return 2 * mu * e + la * e.sum()
+
+    s3 = -2e4
+    s1 = s3 * (1 - sp) / (1 + sp)
+    limit = np.array([s1, s1, s3])
+    for scale, expect_case in ((1.0 - 1e-9, 0), (1.3, 2)):
+        mean = limit.mean()
+        stress = mean + scale * (limit - mean)
+        eps = strain_of(stress)
+        R1, R2 = _rot(rng), _rot(rng)
+        F = R1 @ np.diag(np.exp(eps)) @ R2.T
+        Fo, cs = o.dp_project(F, phi_deg=phi)
+        assert cs == expect_case
+        so = np.sort(stress_of(np.log(np.linalg.svd(Fo, compute_uv=False))))  # ascending: s3 first
+        a3, a1, a2 = so[0], so[1], so[2]
+        assert abs(a1 - a2) < 1e-9 * abs(a3)
+        assert abs((a2 - a3) + (a2 + a3) * sp) < 1e-7 * abs(a3)
