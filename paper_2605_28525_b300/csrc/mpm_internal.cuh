@@ -1,0 +1,254 @@
+// Internal declarations of the sparse-grid MPM library (sm_103a).
+//
+// Data layout in HBM (one context):
+//   particle state   two buffers (ping-pong), each structure-of-arrays with
+//                    NF float components of `pstride` entries: x(3) v(3)
+//                    C(9, row-major) F(9) tau(6, symmetric Kirchhoff stress
+//                    xx xy xz yy yz zz) alpha(1, Drucker-Prager cone constant
+//                    from the friction angle) id(1, uint32 bits).
+//                    G2P reads buffer `cur` through the sort permutation and
+//                    writes buffer 1-cur in sorted (block, cell) order.
+//   hash table       H slots of uint64 keys (EMPTY = all ones) and int32
+//                    values = compact block index Phi (Sec. 4.3, Alg. 5-6).
+//   active list      block_cap entries of (relative block key, slot), sorted
+//                    by key, then block coordinates per Phi.
+//   grid             n_active_blocks * B^3 nodes, node phi = Phi*B^3 + l,
+//                    float4 (m, mv) and float4 (f, 0) accumulators and float4
+//                    (v, m) after the grid update.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/mpm.h"
+
+namespace mpm {
+
+// particle-state component offsets (in units of pstride)
+enum : int {
+    PX = 0, PV = 3, PC = 6, PF = 15, PT = 24, PPHI = 30, PID = 31, NF = 32
+};
+
+constexpr uint64_t EMPTY_KEY = ~0ull;
+constexpr int KEY_BITS = 21;               // m of Eq. (key)
+constexpr int KEY_BIAS = 1 << 20;          // b of Eq. (key)
+
+struct DevStatus {
+    unsigned int n_active;       // Alg. 6 counter
+    unsigned int overflow;       // bit 0: probe limit / table full, bit 1: block capacity
+    unsigned int out_of_domain;
+    unsigned int numeric;        // non-finite state
+    unsigned int n_pblocks;      // blocks holding particles
+    unsigned int map_miss;       // a stencil block missing from the map (must stay 0)
+    unsigned int pad[2];
+};
+
+// Scalar parameters handed to kernels by value.
+struct Params {
+    int lo[3], hi[3];            // node box
+    int blo[3], nb[3];           // block box: first block and block counts
+    float h, inv_h, dt;
+    float g[3];
+    float mu, lambda;            // Lame parameters
+    float mp, V0;                // particle mass and initial volume
+    float phi_deg;
+    int material;
+    int floor_kind;
+    float floor_z, floor_mu;
+    float terrain_mu;
+    int terrain_nx, terrain_ny;
+    const float* terrain;        // device, or nullptr
+    int wall_layers;
+    int block_shift;             // log2(B)
+    int max_probe;
+};
+
+struct HashView {
+    unsigned long long* keys;
+    int* vals;
+    uint64_t mask;               // H - 1
+};
+
+// ------------------------------------------------------------------ keys
+
+// Eq. (key): ((i+b) << 2m) | ((j+b) << m) | (k+b), m = 21, b = 2^20.
+__host__ __device__ inline uint64_t pack_key(int i, int j, int k) {
+    return ((uint64_t)(uint32_t)(i + KEY_BIAS) << (2 * KEY_BITS)) |
+           ((uint64_t)(uint32_t)(j + KEY_BIAS) << KEY_BITS) | (uint64_t)(uint32_t)(k + KEY_BIAS);
+}
+
+// Order-preserving compact key inside the block box (i-major, k fastest).
+__host__ __device__ inline uint32_t rel_key(const Params& P, int bi, int bj, int bk) {
+    return (uint32_t)(((uint64_t)(bi - P.blo[0]) * (uint64_t)P.nb[1] + (uint64_t)(bj - P.blo[1])) *
+                          (uint64_t)P.nb[2] +
+                      (uint64_t)(bk - P.blo[2]));
+}
+
+__host__ __device__ inline void rel_decode(const Params& P, uint32_t r, int& bi, int& bj, int& bk) {
+    bk = (int)(r % (uint32_t)P.nb[2]) + P.blo[2];
+    uint32_t q = r / (uint32_t)P.nb[2];
+    bj = (int)(q % (uint32_t)P.nb[1]) + P.blo[1];
+    bi = (int)(q / (uint32_t)P.nb[1]) + P.blo[0];
+}
+
+// 64-bit finaliser of SplitMix64 (Steele, Lea and Flood 2014), the mixing
+// function the paper names for spreading structured keys over the table.
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+// Lookup of Phi for a block key: linear probing from the hashed slot until the
+// key or an empty slot; bounded by max_probe (Alg. 6 never places a key
+// further than that from its home slot).
+__device__ __forceinline__ int hash_find(const HashView& hv, uint64_t key, int max_probe) {
+    uint64_t s = mix64(key) & hv.mask;
+    for (int r = 0; r < max_probe; ++r) {
+        unsigned long long k = __ldg(&hv.keys[s]);
+        if (k == key) return __ldg(&hv.vals[s]);
+        if (k == EMPTY_KEY) return -1;
+        s = (s + 1) & hv.mask;
+    }
+    return -1;
+}
+
+// ---------------------------------------------------- quadratic B-spline
+
+// Cell/base index: floor(x/h - 1/2).  x/h is exact for power-of-two h and the
+// subtraction of 1/2 is exact for |x/h| < 2^22, so this equals the FP64 value.
+__device__ __forceinline__ int base_index(float fx) { return (int)floorf(fx - 0.5f); }
+
+// Weights of the three stencil nodes base+a for d = x/h - base in [0.5, 1.5):
+// a=0: (1.5-d)^2/2, a=1: 3/4-(d-1)^2, a=2: (d-1/2)^2/2, and their derivatives
+// with respect to x/h.
+__device__ __forceinline__ void bspline3(float d, float w[3], float dw[3]) {
+    float t0 = 1.5f - d, t1 = d - 1.0f, t2 = d - 0.5f;
+    w[0] = 0.5f * t0 * t0;
+    w[1] = 0.75f - t1 * t1;
+    w[2] = 0.5f * t2 * t2;
+    dw[0] = -t0;
+    dw[1] = -2.0f * t1;
+    dw[2] = t2;
+}
+
+__device__ __forceinline__ void bspline_a(float d, int a, float& w, float& dw) {
+    if (a == 0) {
+        float t = 1.5f - d;
+        w = 0.5f * t * t;
+        dw = -t;
+    } else if (a == 1) {
+        float t = d - 1.0f;
+        w = 0.75f - t * t;
+        dw = -2.0f * t;
+    } else {
+        float t = d - 0.5f;
+        w = 0.5f * t * t;
+        dw = t;
+    }
+}
+
+// ------------------------------------------------------------ host side
+
+struct RadixScratch {
+    uint32_t* counts = nullptr;   // [256][ntiles]
+    uint32_t* totals = nullptr;   // [256]
+    int64_t tiles_cap = 0;
+};
+
+}  // namespace mpm
+
+struct mpm_ctx {
+    mpm_config cfg;
+    mpm::Params P;
+    cudaStream_t st = nullptr;
+    int device = 0;
+    bool dense = false, det = false;
+    int B = 4, B3 = 64;
+    int64_t n = 0;
+    int64_t pstride = 0;
+    float* ps[2] = {nullptr, nullptr};
+    int cur = 0;
+
+    // hash + active list
+    unsigned long long* hkeys = nullptr;
+    int* hvals = nullptr;
+    int64_t H = 0;
+    uint32_t* akey[2] = {nullptr, nullptr};
+    uint32_t* aslot[2] = {nullptr, nullptr};
+    int4* bcoord = nullptr;      // per Phi: block coordinates
+    int64_t block_cap = 0;
+    int64_t n_dom_blocks = 0;
+    int64_t n_active = 0;        // blocks after the last rebuild
+    int64_t n_pblocks = 0;
+
+    // per particle
+    uint32_t* pcode = nullptr;   // sparse: slot*B3 + cell; dense: sort key
+    uint32_t* pkey[2] = {nullptr, nullptr};
+    uint32_t* pval[2] = {nullptr, nullptr};
+    int sorted_sel = 0;          // which pkey/pval buffer holds the sorted result
+    int* bstart = nullptr;       // per Phi (first sorted particle of the block)
+    int* bend = nullptr;
+    int* pblocks = nullptr;      // Phi of blocks holding particles
+    int64_t brange_cap = 0;
+    int* cellstart = nullptr;    // deterministic mode: per (Phi, cell) + 1
+    int64_t cellstart_cap = 0;
+
+    // grid
+    float4* gmv = nullptr;
+    float4* gf = nullptr;
+    float4* gv = nullptr;
+    int64_t node_cap = 0;
+
+    // terrain
+    float* terrain = nullptr;
+
+    // status
+    mpm::DevStatus* dstat = nullptr;
+    mpm::DevStatus* hstat = nullptr;   // pinned
+
+    mpm::RadixScratch rs;
+
+    // staging for host <-> device particle copies
+    float* stage = nullptr;
+    int64_t stage_cap = 0;
+
+    int64_t rebuild_rounds = 0;
+    int64_t launches = 0;              // kernels launched by this context
+    int64_t steps = 0;
+    int64_t device_bytes = 0;
+    int phase = 0;                     // 0 idle, 1 rebuilt, 2 p2g done, 3 grid done
+    bool g2p_swapped = false;          // last G2P wrote the buffer now current
+    std::string last_error;
+};
+
+namespace mpm {
+
+// ---- memory (api.cu)
+cudaError_t dalloc(mpm_ctx* c, void** p, size_t bytes);
+void dfree(mpm_ctx* c, void* p, size_t bytes);
+
+// ---- radix sort (radix_sort.cu)
+// Stable LSD sort of (key, value) pairs on `bits` low key bits.  n_dev (device)
+// holds the live count when non-null, clamped to n_cap; otherwise n_cap is the
+// count.  Buffers k[0]/v[0] hold the input; returns the index of the buffer
+// pair that holds the result.
+int radix_sort_pairs(mpm_ctx* c, uint32_t* k[2], uint32_t* v[2], int64_t n_cap,
+                     const unsigned int* n_dev, int bits, cudaStream_t st);
+cudaError_t radix_reserve(mpm_ctx* c, int64_t n_cap);
+
+// ---- rebuild (rebuild.cu)
+cudaError_t launch_insert(mpm_ctx* c);
+cudaError_t launch_dense_codes(mpm_ctx* c);
+cudaError_t launch_assign(mpm_ctx* c);
+cudaError_t launch_particle_keys(mpm_ctx* c);
+cudaError_t launch_ranges(mpm_ctx* c, const uint32_t* skey);
+
+// ---- transfers (transfer.cu)
+cudaError_t launch_p2g(mpm_ctx* c);
+cudaError_t launch_grid_update(mpm_ctx* c);
+cudaError_t launch_g2p(mpm_ctx* c);
+cudaError_t launch_init_stress(mpm_ctx* c, float* buf);
+
+}  // namespace mpm

@@ -153,14 +153,14 @@ def fbm_heightmap(nx: int, ny: int, seed: int = 1, octaves: int = 6, hurst: floa
 
 
 def landslide(seed: int = 0, terrain_seed: int = 1, phi_seed: int = 2, steps: int = 5000,
-              release_cells=(250, 250, 16), grid=(2048, 1024, 256)) -> Workload:
+              release_cells=(250, 250, 16), grid=(2048, 1024, 256), release_x0: int = 100) -> Workload:
     """Slope-aligned frame: x runs down the 35 deg mean slope, gravity is tilted."""
     dx = 0.5
     theta = math.radians(35.0)
     g = (9.81 * math.sin(theta), 0.0, -9.81 * math.cos(theta))
     H = fbm_heightmap(grid[0] + 1, grid[1] + 1, seed=terrain_seed)
     rx, ry, rz = release_cells
-    x0 = 100
+    x0 = release_x0
     y0 = grid[1] // 2 - ry // 2
     # release column (i, j) starts one cell above the highest terrain node of that cell
     hmax = np.maximum.reduce([H[y0:y0 + ry, x0:x0 + rx], H[y0 + 1:y0 + ry + 1, x0:x0 + rx],

@@ -1,0 +1,254 @@
+"""P2G, grid update and G2P on the GPU against the FP64 oracle from identical
+FP32 particle state, element by element.
+
+Tolerances:
+  * m and mv: normwise relative error <= 1e-6 per component family (the bar
+    the method's parity target sets for P2G mass and momentum).
+  * f_int: per node |df| <= 64 u A_n, where u = 2^-24 and
+    A_n = sum_p |grad N|_1 V0 (max|tau_p| + mu + lambda) is the oracle's
+    absolute-value sum: FP32 evaluates tau from a stored FP32 F with absolute
+    error O(u (mu + lambda)) (cancellation in F F^T - I and ln J), and each
+    node sums at most 216 such terms in an arbitrary order.
+  * grid v: |dv| <= 1e-5 (|mv|/m + dt |f|/m + dt |g|) per node: a handful of
+    FP32 roundings of the normalisation and the Euler update.
+  * G2P (one particle from the GPU's own grid velocities): v, x as a few-ulp
+    sum of 27 terms; C scaled by 4/h^2 and F by the gradient sum, bounds in
+    the test body.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2605_28525_b300 import mpm, workloads as W
+from tests.helpers import U32, eq_keys, make_sim, normwise, oracle_for, small_blob, sparse_node_coords
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu_grid(sim, B):
+    sim.rebuild_active()
+    keys = sim.read_active()
+    sim.p2g()
+    g = sim.read_grid()
+    return keys, sparse_node_coords(keys, B), g
+
+
+def _check_p2g(o, wl, x, v, Cm, F, phi, keys, nodes, g, B):
+    m, mv, f = o.p2g(x, v, Cm, F, phi)
+    am, amv, af = o.p2g_abs(x, v, Cm, F, phi)
+    idx = o.node_index(nodes)
+    # the sparse grid covers every node the dense oracle touched
+    assert np.isclose(m[idx].sum(), m.sum(), rtol=1e-13)
+    assert normwise(g["m"], m[idx]) <= 1e-6
+    assert normwise(g["mv"], mv[idx]) <= 1e-6
+    err = np.abs(g["f"].astype(np.float64) - f[idx])
+    assert np.all(err <= 64 * U32 * af[idx] + 1e-30), err.max()
+
+
+@pytest.mark.parametrize("material", [W.NEOHOOKEAN, W.DRUCKER_PRAGER])
+@pytest.mark.parametrize("B", [4, 1])
+@pytest.mark.parametrize("flags", [0, mpm.DETERMINISTIC])
+def test_p2g_parity_random_state(oracle_mod, material, B, flags):
+    wl, Cm, F = small_blob(n=6000, seed=11, material=material, E=1e7, block_size=B)
+    o = oracle_for(wl)
+    sim = mpm.Simulation(mpm.config_from_workload(wl, flags=flags), wl.x, wl.v, Cm, F)
+    keys, nodes, g = _gpu_grid(sim, B)
+    assert np.array_equal(keys, eq_keys(o.active_blocks(wl.x)))
+    _check_p2g(o, wl, wl.x, wl.v, Cm, F, None, keys, nodes, g, B)
+
+
+def test_p2g_parity_per_particle_phi(oracle_mod):
+    wl, Cm, F = small_blob(n=4000, seed=12, material=W.DRUCKER_PRAGER, E=1e7)
+    phi = np.random.default_rng(2).uniform(25, 35, wl.n).astype(np.float32)
+    o = oracle_for(wl)
+    sim = mpm.Simulation(mpm.config_from_workload(wl), wl.x, wl.v, Cm, F, phi)
+    keys, nodes, g = _gpu_grid(sim, 4)
+    _check_p2g(o, wl, wl.x, wl.v, Cm, F, phi, keys, nodes, g, 4)
+
+
+def test_p2g_dense_grid_matches_oracle(oracle_mod):
+    wl, Cm, F = small_blob(n=3000, seed=13)
+    o = oracle_for(wl)
+    sim = mpm.Simulation(mpm.config_from_workload(wl, flags=mpm.DENSE_GRID), wl.x, wl.v, Cm, F)
+    keys, nodes, g = _gpu_grid(sim, 4)
+    m, mv, f = o.p2g(wl.x, wl.v, Cm, F)
+    idx = o.node_index(nodes)
+    inbox = np.all((nodes >= 0) & (nodes <= 32), axis=1)
+    assert np.all(g["m"][~inbox] == 0)
+    assert normwise(g["m"][inbox], m[idx[inbox]]) <= 1e-6
+    assert normwise(g["mv"][inbox], mv[idx[inbox]]) <= 1e-6
+
+
+def test_p2g_mass_conservation_fp32(oracle_mod):
+    wl = W.elastic_cube()
+    sim = make_sim(wl)
+    sim.rebuild_active()
+    sim.p2g()
+    g = sim.read_grid()
+    mp = wl.rho * wl.dx ** 3 / wl.ppc
+    assert abs(g["m"].astype(np.float64).sum() - mp * wl.n) <= 1e-6 * mp * wl.n
+
+
+def test_grid_update_parity(oracle_mod):
+    for floor in (W.FLOOR_STICKY, W.FLOOR_SLIP, W.FLOOR_COULOMB):
+        wl, Cm, F = small_blob(n=5000, seed=14, E=1e6, lo=2, hi=12, vscale=1.0)
+        wl.floor_kind, wl.floor_z, wl.floor_mu = floor, 5 * wl.dx, 0.4
+        o = oracle_for(wl)
+        sim = mpm.Simulation(mpm.config_from_workload(wl), wl.x, wl.v, Cm, F)
+        sim.rebuild_active()
+        keys = sim.read_active()
+        nodes = sparse_node_coords(keys, 4)
+        sim.p2g()
+        sim.grid_update()
+        g = sim.read_grid()
+        for q in range(len(nodes)):
+            mq = float(g["m"][q])
+            want = o.grid_node(nodes[q], mq, g["mv"][q].astype(np.float64), g["f"][q].astype(np.float64))
+            if mq > 0:
+                scale = (np.abs(g["mv"][q]).max() + wl.dt * np.abs(g["f"][q]).max()) / mq + wl.dt * 9.81
+                assert np.all(np.abs(g["v"][q] - want) <= 1e-5 * scale + 1e-12), (nodes[q], g["v"][q], want)
+            else:
+                assert np.all(g["v"][q] == 0)
+
+
+def test_terrain_grid_update_parity(oracle_mod):
+    wl = W.landslide(release_cells=(12, 12, 6), grid=(64, 48, 64), steps=1, release_x0=8)
+    o = oracle_for(wl)
+    sim = make_sim(wl)
+    sim.rebuild_active()
+    nodes = sparse_node_coords(sim.read_active(), 4)
+    sim.p2g()
+    sim.grid_update()
+    g = sim.read_grid()
+    below = 0
+    for q in np.flatnonzero(g["m"] > 0):
+        mq = float(g["m"][q])
+        want = o.grid_node(nodes[q], mq, g["mv"][q].astype(np.float64), g["f"][q].astype(np.float64))
+        scale = (np.abs(g["mv"][q]).max() + wl.dt * np.abs(g["f"][q]).max()) / mq + wl.dt * 9.81
+        assert np.all(np.abs(g["v"][q] - want) <= 1e-5 * scale + 1e-12)
+        below += nodes[q][2] * wl.dx <= wl.terrain[nodes[q][1], nodes[q][0]]
+    assert below > 0
+
+
+@pytest.mark.parametrize("material", [W.NEOHOOKEAN, W.DRUCKER_PRAGER])
+def test_g2p_parity_from_gpu_grid(oracle_mod, material):
+    wl, Cm, F = small_blob(n=3000, seed=15, material=material, E=1e6, fscale=0.01, vscale=0.3, cscale=2.0)
+    o = oracle_for(wl)
+    sim = mpm.Simulation(mpm.config_from_workload(wl), wl.x, wl.v, Cm, F)
+    sim.rebuild_active()
+    nodes = sparse_node_coords(sim.read_active(), 4)
+    sim.p2g()
+    sim.grid_update()
+    g = sim.read_grid()
+    sim.g2p()
+    out = sim.read_particles()
+    lut = {tuple(n): q for q, n in enumerate(nodes)}
+    rng = np.random.default_rng(0)
+    vmax = np.abs(g["v"]).max()
+    h = wl.dx
+    for p in rng.choice(wl.n, 300, replace=False):
+        nd, w, gw = o.weights(wl.x[p].astype(np.float64))
+        v27 = np.array([g["v"][lut[tuple(n)]] for n in nd], np.float64)
+        x1, v1, C1, F1 = o.g2p_one(v27, wl.x[p], F[p])
+        assert np.all(np.abs(out["v"][p] - v1) <= 8 * U32 * vmax + 1e-12)
+        assert np.all(np.abs(out["x"][p] - x1) <= 4 * U32 * np.abs(x1).max() + 8 * U32 * wl.dt * vmax)
+        # C = (4/h^2) sum N v (x) (x_n - x_p): error ~ few u * vmax * (4/h^2) * 1.5 h
+        assert np.all(np.abs(out["C"][p] - C1) <= 64 * U32 * vmax / h + 1e-9)
+        # F = (I + dt L) F with |L| <= 27 vmax |grad N|max ~ 27 vmax / h
+        fb = 16 * U32 * (1 + 27 * wl.dt * vmax / h) * np.abs(F[p]).max()
+        if material == W.NEOHOOKEAN:
+            assert np.all(np.abs(out["F"][p] - F1) <= fb)
+        else:
+            # the return map is Lipschitz in the trial F except at the cone
+            # apex switch; allow a modest amplification
+            assert np.all(np.abs(out["F"][p] - F1) <= 64 * fb + 1e-6)
+
+
+def test_trajectory_elastic_cube_200_steps(oracle_mod):
+    """200 steps of the 32,768-particle elastic cube: FP32 positions within
+    1e-4 of the domain size (1 m) of the FP64 oracle."""
+    wl = W.elastic_cube(steps=200)
+    o = oracle_for(wl)
+    sim = make_sim(wl)
+    sim.step(wl.steps)
+    out = sim.read_particles()
+    x, v, Cm, F = o.run(wl.x, nsteps=wl.steps)
+    L = 1.0
+    err = np.abs(out["x"] - x).max()
+    assert err <= 1e-4 * L, err
+    assert np.abs(out["v"] - v).max() <= 1e-3 * max(np.abs(v).max(), 1e-3)
+    # the cube fell under gravity: z dropped by ~ g t^2 / 2
+    t = wl.steps * wl.dt
+    assert abs((out["x"][:, 2] - wl.x[:, 2]).mean() + 0.5 * 9.81 * t * t) < 0.05 * 0.5 * 9.81 * t * t
+
+
+def test_trajectory_drucker_prager_column(oracle_mod):
+    """A small granular column (DP, Coulomb floor): 100 steps against the
+    oracle; positions within 1e-4 of the 1 m reference length."""
+    wl = W.column_collapse(cells_xy=8, cells_z=24, steps=100)
+    wl.lo, wl.hi = (0, 0, 0), (64, 64, 40)
+    wl.x = wl.x - np.float32((256 - 32) * wl.dx) * np.array([1, 1, 0], np.float32)
+    o = oracle_for(wl)
+    sim = make_sim(wl)
+    sim.step(wl.steps)
+    out = sim.read_particles()
+    x, v, Cm, F = o.run(wl.x, nsteps=wl.steps)
+    assert np.abs(out["x"] - x).max() <= 1e-4
+
+
+def test_sparse_equals_dense_bitwise(oracle_mod):
+    """Deterministic mode: GPU sparse and GPU dense give identical bits at every
+    step (the paper's 'identical results' claim)."""
+    wl = W.elastic_cube(steps=30)
+    wl.v = np.tile(np.array([[0.6, -0.4, 0.2]], np.float32), (wl.n, 1))
+    a = make_sim(wl, flags=mpm.DETERMINISTIC)
+    b = make_sim(wl, flags=mpm.DETERMINISTIC | mpm.DENSE_GRID)
+    for step in range(wl.steps):
+        a.step(1)
+        b.step(1)
+        pa, pb = a.read_particles(), b.read_particles()
+        for k in ("x", "v", "C", "F"):
+            assert np.array_equal(pa[k].view(np.uint32), pb[k].view(np.uint32)), (step, k)
+
+
+def test_sparse_equals_dense_bitwise_dp(oracle_mod):
+    wl = W.column_collapse(cells_xy=8, cells_z=16, steps=20)
+    a = make_sim(wl, flags=mpm.DETERMINISTIC)
+    b = make_sim(wl, flags=mpm.DETERMINISTIC | mpm.DENSE_GRID)
+    a.step(wl.steps)
+    b.step(wl.steps)
+    pa, pb = a.read_particles(), b.read_particles()
+    for k in ("x", "v", "C", "F"):
+        assert np.array_equal(pa[k].view(np.uint32), pb[k].view(np.uint32)), k
+
+
+def test_deterministic_repeatable_and_restart(oracle_mod):
+    wl = W.elastic_cube(steps=20)
+    wl.v = np.tile(np.array([[0.3, 0.1, -0.2]], np.float32), (wl.n, 1))
+    a = make_sim(wl, flags=mpm.DETERMINISTIC)
+    a.step(10)
+    mid = a.read_particles()
+    a.step(10)
+    end_a = a.read_particles()
+    # restart from the checkpoint (state in id order)
+    b = mpm.Simulation(mpm.config_from_workload(wl, flags=mpm.DETERMINISTIC), mid["x"], mid["v"],
+                       mid["C"].reshape(-1, 9), mid["F"].reshape(-1, 9))
+    b.step(10)
+    end_b = b.read_particles()
+    # write_particles on a live context restores the same checkpoint
+    a.write_particles(mid["x"], mid["v"], mid["C"].reshape(-1, 9), mid["F"].reshape(-1, 9))
+    a.step(10)
+    end_c = a.read_particles()
+    for k in ("x", "v", "C", "F"):
+        assert np.array_equal(end_a[k].view(np.uint32), end_b[k].view(np.uint32)), k
+        assert np.array_equal(end_a[k].view(np.uint32), end_c[k].view(np.uint32)), k
+
+
+def test_fast_mode_close_to_deterministic(oracle_mod):
+    wl = W.elastic_cube(steps=20)
+    a = make_sim(wl)
+    b = make_sim(wl, flags=mpm.DETERMINISTIC)
+    a.step(20)
+    b.step(20)
+    assert np.abs(a.read_particles()["x"] - b.read_particles()["x"]).max() <= 1e-6
