@@ -1,0 +1,368 @@
+"""Throughput of the sparse-grid MPM step on B300 (particle-updates/s).
+
+One "step" is one full explicit MPM step through the C-ABI: the active-set
+rebuild (cell keys, hashed insert, compaction, particle sort), P2G, the grid
+update and G2P with the Drucker-Prager return map.  The default workload is
+the 1,048,576-particle granular column collapse (512x512x256 potential grid,
+dx = 1/128).  All inputs are synthetic and seeded.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl b300|reference]
+
+Rank 0 prints ONE JSON line.  Under torchrun every rank runs an independent
+replica (the method does not shard across GPUs); value = all particles of all
+ranks x K / max-over-ranks timed seconds.  `--impl reference` times the FP64
+CPU oracle (the plain, slow dense-grid implementation the tests check
+against) on the same workload, K bounded steps after W warm-up steps.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particle-updates/s per MPM step incl. sparse rebuild, vs dense-grid GPU path"
+UNIT = "particle-updates/s"
+
+# Algorithmic bytes per particle of the dominant kernels (FP32 state, the
+# figures of the method's byte model): P2G reads x, v, C, F (96 B); G2P reads
+# x, F and writes x, v, C, F (144 B).  The grid traffic of the active nodes is
+# added per node (P2G: 28 B of m, mv, f accumulated; G2P: 12 B of v read).
+ALG_BYTES = {"p2g": (96, 28), "g2p": (144, 12)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _init_pg(ws, backend):
+    if ws <= 1:
+        return None
+    import torch.distributed as dist
+    if not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def max_over_ranks(value: float, dist=None, device=None) -> float:
+    """Max of a scalar over all ranks (identity without a process group)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(value: float, dist=None, device=None) -> float:
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def measured_traffic(workload: str, kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernel source changed after the counters were taken."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2605_28525_b300", "csrc", "transfer.cu")
+    try:
+        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+        for line in open(os.path.join(ROOT, "profiles", "traffic.txt")):
+            f = line.split()
+            if len(f) == 4 and not line.startswith("#") and f[0] == workload and f[1] == kernel and f[3] == sha:
+                return int(f[2])
+    except OSError:
+        pass
+    return None
+
+
+def make_workload(name: str):
+    from paper_2605_28525_b300 import workloads as W
+    if name == "column_collapse_1M":
+        return W.column_collapse()
+    if name == "column_collapse_4M":
+        return W.column_collapse(cells_xy=64)
+    if name == "landslide_8M":
+        return W.landslide()
+    if name == "elastic_cube_32k":
+        return W.elastic_cube()
+    raise SystemExit("unknown workload %s" % name)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = "/tmp/mpm_bench_clocks_%d_%d.csv" % (os.getpid(), index)
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            self.proc.wait(timeout=10)
+            self.f.close()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except OSError:
+            return None
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def time_steps(sim, nsteps, flush=None):
+    """Per-step device time (ms) of sim.step(1) with CUDA events on the
+    library's stream; the L2 is flushed between steps outside the events."""
+    import torch
+    st = torch.cuda.current_stream()
+    out = []
+    for _ in range(nsteps):
+        if flush is not None:
+            flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        sim.step(1)
+        b.record(st)
+        b.synchronize()
+        out.append(a.elapsed_time(b))
+    return out
+
+
+def time_phases(sim, nsteps, flush=None):
+    """Device time (ms) of each phase of the step, through the phase entry
+    points (same kernels as sim.step)."""
+    import torch
+    st = torch.cuda.current_stream()
+    acc = {"rebuild": [], "p2g": [], "grid": [], "g2p": []}
+    for _ in range(nsteps):
+        if flush is not None:
+            flush.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        ev[0].record(st)
+        sim.rebuild_active()
+        ev[1].record(st)
+        sim.p2g()
+        ev[2].record(st)
+        sim.grid_update()
+        ev[3].record(st)
+        sim.g2p()
+        ev[4].record(st)
+        ev[4].synchronize()
+        for k, name in enumerate(("rebuild", "p2g", "grid", "g2p")):
+            acc[name].append(ev[k].elapsed_time(ev[k + 1]))
+    return {k: float(np.mean(v)) for k, v in acc.items()}
+
+
+def e2e_steps(sim, n, nsteps):
+    """End-to-end through the public API with host buffers: each step uploads
+    the particle state from pinned host memory, steps, and reads it back."""
+    import torch
+    pin = lambda *s: torch.empty(*s, dtype=torch.float32, pin_memory=True).numpy()
+    state = sim.read_particles({"x": pin(n, 3), "v": pin(n, 3), "C": pin(n, 3, 3), "F": pin(n, 3, 3)})
+    out = {"x": pin(n, 3), "v": pin(n, 3), "C": pin(n, 3, 3), "F": pin(n, 3, 3)}
+    ts = []
+    for _ in range(nsteps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.write_particles(state["x"], state["v"], state["C"].reshape(n, 9), state["F"].reshape(n, 9))
+        sim.step(1)
+        sim.read_particles(out)
+        ts.append(time.perf_counter() - t0)
+        state, out = out, state
+    h2d = n * (3 + 3 + 9 + 9) * 4
+    return float(np.mean(ts)), h2d, h2d
+
+
+def cpu_baseline(wl, nsteps):
+    """The FP64 oracle as it stands, one host core, on `nsteps` full steps of
+    the same workload (its dense grid covers the whole potential box)."""
+    import oracle
+    o = oracle.Oracle(lo=wl.lo, hi=wl.hi, h=wl.dx, dt=wl.dt, g=wl.gravity, B=wl.block_size, material=wl.material,
+                      E=wl.E, nu=wl.nu, rho=wl.rho, phi_deg=wl.phi_deg, ppc=wl.ppc, floor_kind=wl.floor_kind,
+                      floor_z=wl.floor_z, floor_mu=wl.floor_mu,
+                      terrain=None if wl.terrain is None else wl.terrain.astype(np.float64),
+                      terrain_mu=wl.terrain_mu, wall_layers=wl.wall_layers)
+    t0 = time.perf_counter()
+    o.run(wl.x, wl.v, None, None, wl.phi, nsteps=nsteps)
+    dt = time.perf_counter() - t0
+    return wl.n * nsteps / dt, dt
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    wl = make_workload(args.workload)
+    import oracle
+    o_args = dict(lo=wl.lo, hi=wl.hi, h=wl.dx, dt=wl.dt, g=wl.gravity, B=wl.block_size, material=wl.material,
+                  E=wl.E, nu=wl.nu, rho=wl.rho, phi_deg=wl.phi_deg, ppc=wl.ppc, floor_kind=wl.floor_kind,
+                  floor_z=wl.floor_z, floor_mu=wl.floor_mu, wall_layers=wl.wall_layers)
+    o = oracle.Oracle(**o_args)
+    x, v, Cm, F = o.run(wl.x, wl.v, None, None, wl.phi, nsteps=args.warmup)
+    t0 = time.perf_counter()
+    o.run(x, v, Cm, F, wl.phi, nsteps=args.steps)
+    dt = time.perf_counter() - t0
+    value = wl.n * args.steps / dt
+    sample = "%d full FP64 oracle steps of %s (%d particles, dense %s node grid) after %d warm-up steps" % (
+        args.steps, wl.name, wl.n, "x".join(str(wl.hi[a] - wl.lo[a] + 1) for a in range(3)), args.warmup)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": dict(wl.describe(), l2="n/a (host)"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
+    ap.add_argument("--workload", default="column_collapse_1M")
+    ap.add_argument("--dense-steps", type=int, default=5)
+    ap.add_argument("--cpu-steps", type=int, default=3)
+    ap.add_argument("--no-dense", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-flush", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    ws, rank, local = _dist()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+
+    import torch
+    from paper_2605_28525_b300 import mpm, workloads as W
+    torch.cuda.set_device(local)
+    dist = _init_pg(ws, "nccl")
+    dev = torch.device("cuda", local)
+    wl = make_workload(args.workload)
+    flush = None if args.no_flush else torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    sim = mpm.Simulation.from_workload(wl, stream=stream, device_inputs=True)
+    for _ in range(args.warmup):
+        sim.step(1)
+    torch.cuda.synchronize()
+    launches0 = sim.stats()["kernel_launches"]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        per_step = time_steps(sim, args.steps, flush)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    launches = sim.stats()["kernel_launches"] - launches0
+    total_ms = max_over_ranks(sum(per_step), dist, dev)
+    n_all = sum_over_ranks(wl.n, dist, dev)
+    value = n_all * args.steps / (total_ms / 1e3)
+    st = sim.stats()
+
+    phases = time_phases(sim, max(3, min(args.steps, 10)), flush)
+    dom = max(("p2g", "g2p"), key=lambda k: phases[k])
+    pb, nb = ALG_BYTES[dom]
+    alg_bytes = wl.n * pb + st["n_active_nodes"] * nb
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6400.0))
+    achieved = alg_bytes / (phases[dom] * 1e-3) / 1e9
+    traffic = measured_traffic(wl.name, dom)
+
+    e2e = None
+    if not args.no_e2e:
+        t_e2e, h2d, d2h = e2e_steps(sim, wl.n, max(3, min(args.steps, 5)))
+        e2e = {"value": wl.n * ws / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    sim.close()
+
+    dense = None
+    if not args.no_dense:
+        dsim = mpm.Simulation.from_workload(wl, flags=mpm.DENSE_GRID, stream=stream, device_inputs=True)
+        for _ in range(3):
+            dsim.step(1)
+        d_ms = time_steps(dsim, args.dense_steps, flush)
+        dsim.close()
+        dense_value = wl.n / (np.mean(d_ms) / 1e3)
+        dense = {"value": dense_value * ws, "unit": UNIT, "ms_per_step": float(np.mean(d_ms)),
+                 "sparse_speedup": (wl.n / (total_ms / args.steps / 1e3)) / dense_value,
+                 "occupancy_nodes": st["n_active_nodes"] / st["n_dense_nodes"]}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cv, cdt = cpu_baseline(wl, args.cpu_steps)
+        cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "%d full FP64 oracle steps of %s (%d particles, dense %s node grid), %.1f s" % (
+                   args.cpu_steps, wl.name, wl.n, "x".join(str(wl.hi[a] - wl.lo[a] + 1) for a in range(3)), cdt)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(wl.describe(), l2="flushed between steps" if flush is not None else "not flushed",
+                           parallelism="replicas" if ws > 1 else "single GPU",
+                           active_blocks=st["n_active_blocks"], particle_blocks=st["n_particle_blocks"]),
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                         "alg_bytes_per_launch": alg_bytes, "kernel_ms": phases[dom]},
+            "phases_ms": phases,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "dense_gpu": dense,
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
