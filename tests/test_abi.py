@@ -1,0 +1,90 @@
+"""The C-ABI library loads on a CPU-only host, exports every function that
+include/mpm.h declares, and rejects invalid configurations before touching
+the GPU (no compute calls here)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def native():
+    from paper_2605_28525_b300 import build, mpm
+    build.build()
+    return mpm
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "mpm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:mpm_status|const char\s*\*|void)\s+(mpm_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("mpm_create", "mpm_rebuild_active", "mpm_step", "mpm_read_particles", "mpm_destroy"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(native):
+    lib = C.CDLL(native.LIB_PATH)
+    names = _declared_functions()
+    assert names == sorted(native.EXPORTS)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_status_strings(native):
+    L = native.lib()
+    seen = set()
+    for s in range(8):
+        txt = L.mpm_status_string(s).decode()
+        assert txt and txt not in seen
+        seen.add(txt)
+    assert L.mpm_status_string(99).decode() == "unknown status"
+
+
+def _try_create(native, **over):
+    cfg = native.default_config()
+    for k, v in over.items():
+        if k in ("domain_lo", "domain_hi", "gravity"):
+            getattr(cfg, k)[:] = v
+        else:
+            setattr(cfg, k, v)
+    x = np.full((4, 3), 0.5, np.float32)
+    h = C.c_void_p()
+    st = native.lib().mpm_create(C.byref(cfg), over.get("_n", 4), x.ctypes.data_as(C.c_void_p), None, None, None,
+                                 None, 0, None, C.byref(h))
+    return st, native.lib().mpm_last_error(None).decode()
+
+
+@pytest.mark.parametrize("over, why", [
+    (dict(dx=0.03), "power of two"),
+    (dict(block_size=3), "block_size"),
+    (dict(dt=0.0), "dt"),
+    (dict(nu=0.5), "nu"),
+    (dict(rho=0.0), "rho"),
+    (dict(material=7), "material"),
+    (dict(floor_kind=9), "floor"),
+    (dict(hash_capacity=100), "power of two"),
+    (dict(domain_lo=[0, 0, 0], domain_hi=[2, 64, 64]), "3 cells"),
+    (dict(domain_lo=[-(1 << 20) - 1, 0, 0]), "Eq. (key)"),
+    (dict(domain_lo=[0, 0, 0], domain_hi=[1 << 19, 1 << 19, 1 << 10]), "2^32"),
+    (dict(_n=0), "particle count"),
+])
+def test_invalid_configs_rejected_on_host(native, over, why):
+    st, msg = _try_create(native, **over)
+    assert st == native.ERR_INVALID_ARG
+    assert why in msg, msg
+
+
+def test_python_binding_raises_without_library(monkeypatch, tmp_path):
+    from paper_2605_28525_b300 import mpm
+    monkeypatch.setattr(mpm, "_lib", None)
+    monkeypatch.setattr(mpm, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(ImportError):
+        mpm.lib()

@@ -1,0 +1,63 @@
+"""Host-side pieces that need no GPU: workload generators, key packing helpers
+and the bench's reporting helpers."""
+import math
+
+import numpy as np
+
+from paper_2605_28525_b300 import mpm, workloads as W
+
+
+def test_elastic_cube_shape():
+    wl = W.elastic_cube()
+    assert wl.n == 16 ** 3 * 8 == 32768 and wl.x.dtype == np.float32
+    c = np.floor(wl.x / np.float32(wl.dx)).astype(int)
+    assert c.min() == 24 and c.max() == 39
+    counts = np.unique(c[:, 0] * 4096 + c[:, 1] * 64 + c[:, 2], return_counts=True)[1]
+    assert np.all(counts == 8)                                   # 8 particles per cell
+
+
+def test_column_collapse_counts():
+    assert W.column_collapse().n == 1_048_576
+    assert W.column_collapse(cells_xy=64).n == 4_194_304
+    wl = W.column_collapse()
+    z = wl.x[:, 2] / wl.dx
+    assert z.min() >= 3.0 and z.max() <= 131.0 and abs(wl.x[:, 0].mean() - 2.0) < 1e-3
+
+
+def test_landslide_small_is_above_terrain_and_seeded():
+    a = W.landslide(release_cells=(20, 16, 4), grid=(128, 64, 96), release_x0=10)
+    b = W.landslide(release_cells=(20, 16, 4), grid=(128, 64, 96), release_x0=10)
+    assert np.array_equal(a.x, b.x) and np.array_equal(a.phi, b.phi)
+    assert a.n == 20 * 16 * 4 * 8
+    assert 25.0 <= a.phi.min() and a.phi.max() <= 35.0
+    i = np.floor(a.x[:, 0] / a.dx).astype(int)
+    j = np.floor(a.x[:, 1] / a.dx).astype(int)
+    hmax = np.maximum.reduce([a.terrain[j, i], a.terrain[j + 1, i], a.terrain[j, i + 1], a.terrain[j + 1, i + 1]])
+    assert np.all(a.x[:, 2] > hmax)
+    g = np.array(a.gravity)
+    assert abs(np.linalg.norm(g) - 9.81) < 1e-9 and abs(math.degrees(math.atan2(g[0], -g[2])) - 35.0) < 1e-9
+
+
+def test_fbm_statistics():
+    H = W.fbm_heightmap(257, 129, seed=1)
+    assert abs(H.mean() - 8.0) < 1e-3 and abs(H.std() - 4.0) < 1e-3
+    assert np.array_equal(H, W.fbm_heightmap(257, 129, seed=1))
+    assert not np.array_equal(H, W.fbm_heightmap(257, 129, seed=2))
+
+
+def test_unpack_keys_roundtrip():
+    rng = np.random.default_rng(0)
+    b = rng.integers(-(1 << 20), (1 << 20) - 1, size=(1000, 3))
+    keys = ((b[:, 0] + (1 << 20)) << 42 | (b[:, 1] + (1 << 20)) << 21 | (b[:, 2] + (1 << 20))).astype(np.uint64)
+    assert np.array_equal(mpm.unpack_keys(keys), b)
+
+
+def test_bench_traffic_lookup_and_clock_summary(tmp_path):
+    import bench
+    assert bench.measured_traffic("no_such_workload", "p2g") is None
+    s = bench.ClockSampler(0)
+    s.path = str(tmp_path / "c.csv")
+    open(s.path, "w").write("0, 1900, 2032, 700, 0x0, Not Active, Not Active, Not Active, Active\n"
+                            "0, 1950, 2032, 710, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+    out = s.summary()
+    assert out["sm_mhz"] == 1925.0 and out["sm_max_mhz"] == 2032.0 and out["reasons"] == ["sw_power_cap"]
