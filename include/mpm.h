@@ -52,7 +52,8 @@ typedef enum {
     MPM_ERR_HASH_OVERFLOW = 3, /* Alg. 7 regrowth still overflowed after max_rebuilds */
     MPM_ERR_OUT_OF_DOMAIN = 4, /* a stencil node left the potential grid box */
     MPM_ERR_NUMERIC = 5,       /* non-finite state or J <= 0; state rolled back */
-    MPM_ERR_CUDA = 6,          /* a CUDA runtime call failed (see mpm_last_error) */
+    MPM_ERR_CUDA = 6,          /* a CUDA runtime call failed, or device work did not finish
+                                  within 20 s of a wait (see mpm_last_error) */
     MPM_ERR_STATE = 7          /* call out of order (e.g. mpm_p2g before a rebuild) */
 } mpm_status;
 
@@ -62,7 +63,7 @@ enum { MPM_FLOOR_NONE = 0, MPM_FLOOR_STICKY = 1, MPM_FLOOR_SLIP = 2, MPM_FLOOR_C
 /* mpm_config.flags */
 #define MPM_DETERMINISTIC 1u /* fixed-order P2G reduction and (block, cell, id) particle order:
                                 results are bit-reproducible and identical between the sparse
-                                and the dense grid */
+                                and the dense grid; needs block_size 4 */
 #define MPM_DENSE_GRID 2u    /* comparator: identity map over every block of the box; the grid
                                 is cleared and updated over the whole potential domain */
 

@@ -21,7 +21,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmpm_b300.so")
 HEADERS = [os.path.join(ROOT, "include", "mpm.h"), os.path.join(CSRC, "mpm_internal.cuh")]
-NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
+NVCC = "/usr/local/cuda/bin/nvcc"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-Xptxas", "-warn-spills"]
@@ -38,26 +38,29 @@ def _newer(src_list, target):
     return any(os.path.getmtime(s) > t for s in src_list)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(OBJ, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, out: str = LIB, obj_dir: str = OBJ, defines=()) -> str:
+    """Compile every csrc/*.cu and link `out`.  `defines` (e.g. ("MPM_SVD_SWEEPS=4",))
+    and a separate `obj_dir` build variants side by side."""
+    os.makedirs(obj_dir, exist_ok=True)
+    extra = ["-D" + d for d in defines]
     objs = []
     for src in sources():
-        obj = os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(obj_dir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if force or _newer([src] + HEADERS, obj):
-            cmd = [NVCC] + ARCH + FLAGS + ["-c", src, "-o", obj]
+            cmd = [NVCC] + ARCH + FLAGS + extra + ["-c", src, "-o", obj]
             if verbose:
                 print(" ".join(cmd), flush=True)
             subprocess.check_call(cmd)
-    if force or _newer(objs, LIB):
-        tmp = LIB + ".tmp%d" % os.getpid()
+    if force or _newer(objs, out):
+        tmp = out + ".tmp%d" % os.getpid()
         cmd = [NVCC] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + \
               ["-Xlinker", "-rpath,/usr/local/cuda/lib64"]
         if verbose:
             print(" ".join(cmd), flush=True)
         subprocess.check_call(cmd)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, out)
+    return out
 
 
 if __name__ == "__main__":

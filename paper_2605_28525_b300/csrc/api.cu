@@ -13,6 +13,8 @@
 #include <cstring>
 #include <unordered_map>
 #include <vector>
+#include <chrono>
+#include <thread>
 
 #include "mpm_internal.cuh"
 
@@ -124,6 +126,8 @@ mpm_status validate(const mpm_config* cfg, int64_t n) {
     if (!cfg) return fail(nullptr, MPM_ERR_INVALID_ARG, "cfg is NULL");
     if (n < 1 || n > (int64_t)INT32_MAX) return fail(nullptr, MPM_ERR_INVALID_ARG, "particle count out of range");
     if (cfg->block_size != 1 && cfg->block_size != 4) return fail(nullptr, MPM_ERR_INVALID_ARG, "block_size must be 1 or 4");
+    if ((cfg->flags & MPM_DETERMINISTIC) && cfg->block_size != 4)
+        return fail(nullptr, MPM_ERR_INVALID_ARG, "MPM_DETERMINISTIC needs block_size 4");
     if (!(cfg->dx > 0.0) || !std::isfinite(cfg->dx)) return fail(nullptr, MPM_ERR_INVALID_ARG, "dx must be positive");
     int ex;
     if (std::frexp(cfg->dx, &ex) != 0.5) return fail(nullptr, MPM_ERR_INVALID_ARG, "dx must be a power of two");
@@ -162,10 +166,22 @@ mpm_status validate(const mpm_config* cfg, int64_t n) {
     return MPM_OK;
 }
 
+// Wait for the context's stream, giving up after a fixed time so that a
+// stalled device reports an error instead of blocking the caller forever.
+cudaError_t sync_wait(mpm_ctx* c) {
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaStreamQuery(c->st);
+        if (e != cudaErrorNotReady) return e;
+        if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(20)) return cudaErrorLaunchTimeout;
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+}
+
 cudaError_t read_status(mpm_ctx* c) {
     cudaError_t e = cudaMemcpyAsync(c->hstat, c->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->st);
     if (e != cudaSuccess) return e;
-    return cudaStreamSynchronize(c->st);
+    return sync_wait(c);
 }
 
 cudaError_t alloc_hash(mpm_ctx* c, int64_t H, int64_t cap) {
@@ -214,7 +230,10 @@ cudaError_t ensure_block_arrays(mpm_ctx* c, int64_t nb) {
     dfree(c, c->bend, 0);
     dfree(c, c->pblocks, 0);
     dfree(c, c->bcoord, 0);
-    c->bstart = c->bend = c->pblocks = nullptr;
+    dfree(c, c->nbr, 0);
+    dfree(c, c->ccount, 0);
+    dfree(c, c->hasp, 0);
+    c->bstart = c->bend = c->pblocks = c->nbr = c->ccount = c->hasp = nullptr;
     c->bcoord = nullptr;
     c->brange_cap = 0;
     cudaError_t e;
@@ -222,6 +241,12 @@ cudaError_t ensure_block_arrays(mpm_ctx* c, int64_t nb) {
     if ((e = dalloc(c, (void**)&c->bend, sizeof(int) * nc)) != cudaSuccess) return e;
     if ((e = dalloc(c, (void**)&c->pblocks, sizeof(int) * nc)) != cudaSuccess) return e;
     if ((e = dalloc(c, (void**)&c->bcoord, sizeof(int4) * nc)) != cudaSuccess) return e;
+    if (!c->dense && (e = dalloc(c, (void**)&c->nbr, sizeof(int) * nc * (c->B == 4 ? 8 : 27))) != cudaSuccess)
+        return e;
+    if ((e = dalloc(c, (void**)&c->ccount, sizeof(int) * nc * c->B3)) != cudaSuccess) return e;
+    if ((e = dalloc(c, (void**)&c->hasp, sizeof(int) * nc)) != cudaSuccess) return e;
+    // generation 0 never matches a live step: start from a clean table
+    if ((e = cudaMemsetAsync(c->hasp, 0, sizeof(int) * nc, c->st)) != cudaSuccess) return e;
     c->brange_cap = nc;
     return cudaSuccess;
 }
@@ -245,7 +270,11 @@ mpm_status do_rebuild(mpm_ctx* c) {
         else CK(launch_insert(c));
         CK(read_status(c));
         const DevStatus& s = *c->hstat;
-        if (s.map_miss) return fail(c, MPM_ERR_CUDA, "internal error: a stencil block was missing from the map");
+        if (s.map_miss) {
+            cudaMemsetAsync(&c->dstat->map_miss, 0, sizeof(unsigned int), c->st);
+            return fail(c, MPM_ERR_CUDA, "internal error: inconsistent active map or particle order (code " +
+                                             std::to_string(s.map_miss) + ")");
+        }
         if (s.numeric) {
             rollback_g2p(c);
             return fail(c, MPM_ERR_NUMERIC, "non-finite or inverted particle state");
@@ -267,7 +296,8 @@ mpm_status do_rebuild(mpm_ctx* c) {
     const int64_t nodes = c->n_active * c->B3;
     CK(ensure_grid(c, nodes));
     CK(ensure_block_arrays(c, c->n_active));
-    if (c->det) CK(grow(c, c->cellstart, c->cellstart_cap, nodes + 1, 1.25));
+    if (c->det) CK(grow(c, c->tbuf, c->tbuf_cap, c->n_active * 7 * 216, 1.25));
+    ++c->gen;
     CK(launch_assign(c));
     CK(launch_particle_keys(c));
     CK(launch_ranges(c, c->pkey[c->sorted_sel]));
@@ -299,7 +329,12 @@ mpm_status do_g2p(mpm_ctx* c) {
 // Check the flags of the last G2P (one status read).
 mpm_status settle(mpm_ctx* c) {
     CK(read_status(c));
-    if (c->hstat->map_miss) return fail(c, MPM_ERR_CUDA, "internal error: a stencil block was missing from the map");
+    if (c->hstat->map_miss) {
+        const unsigned code = c->hstat->map_miss;
+        cudaMemsetAsync(&c->dstat->map_miss, 0, sizeof(unsigned int), c->st);
+        return fail(c, MPM_ERR_CUDA, "internal error: inconsistent active map or particle order (code " +
+                                         std::to_string(code) + ")");
+    }
     if (c->hstat->numeric) {
         rollback_g2p(c);
         return fail(c, MPM_ERR_NUMERIC, "non-finite or inverted particle state");
@@ -586,7 +621,7 @@ mpm_status mpm_read_particles(mpm_ctx* c, float* x, float* v, float* Cm, float* 
         if (!on_device)
             CK(cudaMemcpyAsync(it.dst, c->stage, sizeof(float) * c->n * it.ncomp, cudaMemcpyDeviceToHost, c->st));
     }
-    CK(cudaStreamSynchronize(c->st));
+    CK(sync_wait(c));
     return MPM_OK;
 }
 
@@ -628,7 +663,7 @@ mpm_status mpm_read_active(mpm_ctx* c, uint64_t* keys, int64_t cap, int64_t* n_o
     std::vector<int4> bc(c->n_active);
     if (c->n_active) {
         CK(cudaMemcpyAsync(bc.data(), c->bcoord, sizeof(int4) * c->n_active, cudaMemcpyDeviceToHost, c->st));
-        CK(cudaStreamSynchronize(c->st));
+        CK(sync_wait(c));
     }
     for (int64_t r = 0; r < c->n_active; ++r) keys[r] = pack_key(bc[r].x, bc[r].y, bc[r].z);
     return MPM_OK;
@@ -644,7 +679,7 @@ mpm_status mpm_read_grid(mpm_ctx* c, float* m, float* mv, float* f, float* v, in
         CK(cudaMemcpyAsync(a.data(), c->gmv, sizeof(float4) * nn, cudaMemcpyDeviceToHost, c->st));
         CK(cudaMemcpyAsync(b.data(), c->gf, sizeof(float4) * nn, cudaMemcpyDeviceToHost, c->st));
         CK(cudaMemcpyAsync(g.data(), c->gv, sizeof(float4) * nn, cudaMemcpyDeviceToHost, c->st));
-        CK(cudaStreamSynchronize(c->st));
+        CK(sync_wait(c));
     }
     for (int64_t i = 0; i < nn; ++i) {
         if (m) m[i] = a[i].x;
@@ -675,7 +710,7 @@ mpm_status mpm_get_stats(mpm_ctx* c, mpm_stats* o) {
     o->n_active_nodes = c->n_active * c->B3;
     if (c->phase >= 1 || c->steps > 0) {
         CK(cudaMemcpyAsync(c->hstat, c->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->st));
-        CK(cudaStreamSynchronize(c->st));
+        CK(sync_wait(c));
         o->n_particle_blocks = c->hstat->n_pblocks;
     }
     int64_t dn = 1;
@@ -694,7 +729,7 @@ mpm_status mpm_get_stats(mpm_ctx* c, mpm_stats* o) {
 
 void mpm_destroy(mpm_ctx* c) {
     if (!c) return;
-    cudaStreamSynchronize(c->st);
+    (void)sync_wait(c);
     auto it = registries().find(c);
     if (it != registries().end()) {
         for (auto& kv : it->second.sizes) {

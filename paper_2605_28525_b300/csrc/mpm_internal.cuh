@@ -191,9 +191,13 @@ struct mpm_ctx {
     int* bstart = nullptr;       // per Phi (first sorted particle of the block)
     int* bend = nullptr;
     int* pblocks = nullptr;      // Phi of blocks holding particles
+    int* ccount = nullptr;       // per (Phi, cell): particles in the cell (k-major P2G order)
+    int* nbr = nullptr;          // per Phi: Phi of the blocks b + {0..R-1}^3 (R = 2 for B = 4, 3 for B = 1)
     int64_t brange_cap = 0;
-    int* cellstart = nullptr;    // deterministic mode: per (Phi, cell) + 1
-    int64_t cellstart_cap = 0;
+    float* tbuf = nullptr;       // deterministic mode: 7 x 216 tile floats per block
+    int64_t tbuf_cap = 0;
+    int* hasp = nullptr;         // per Phi: generation of the last step the block held particles
+    int gen = 0;                 // rebuild generation
 
     // grid
     float4* gmv = nullptr;

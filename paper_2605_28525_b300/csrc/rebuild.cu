@@ -16,8 +16,9 @@
 //   k_particle_keys   sort key (Phi(b(base)), l(base)) per particle.
 //   k_ranges          particle range of every block that holds particles and
 //                     the list of such blocks.
-//   k_cellstart       first sorted particle of every (Phi, cell) (fixed-order
-//                     P2G only).
+//   k_interleave      k-major particle order inside every block (the k-th
+//                     particle of each cell, then the next), and the particle
+//                     count per cell, for the cell-lane P2G.
 #include "mpm_internal.cuh"
 
 namespace mpm {
@@ -37,7 +38,6 @@ __global__ void k_hash_clear(unsigned long long* __restrict__ keys, int* __restr
         st->overflow = 0;
         st->out_of_domain = 0;
         st->n_pblocks = 0;
-        st->map_miss = 0;
     }
 }
 
@@ -46,7 +46,6 @@ __global__ void k_status_clear(DevStatus* st) {
     st->overflow = 0;
     st->out_of_domain = 0;
     st->n_pblocks = 0;
-    st->map_miss = 0;
 }
 
 // Alg. 6 for one key; returns the slot holding it or -1 when n_probe slots
@@ -176,6 +175,21 @@ __global__ void k_assign(const uint32_t* __restrict__ skey, const uint32_t* __re
     }
 }
 
+// Phi of the blocks b + {0..R-1}^3 of every active block (runs after
+// k_assign, once every table value holds its rank).
+template <int B>
+__global__ void k_neighbours(const int4* __restrict__ bcoord, int64_t nact, Params P, HashView hv,
+                             int* __restrict__ nbr) {
+    constexpr int R = (B == 4) ? 2 : 3;
+    constexpr int NNB = R * R * R;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nact * NNB) return;
+    const int64_t r = t / NNB;
+    const int e = (int)(t % NNB);
+    const int4 b = bcoord[r];
+    nbr[t] = hash_find(hv, pack_key(b.x + e / (R * R), b.y + (e / R) % R, b.z + e % R), P.max_probe);
+}
+
 __global__ void k_zero_grid(float4* __restrict__ gmv, float4* __restrict__ gf, int64_t nn) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (int64_t)gridDim.x * blockDim.x) {
         gmv[i] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -211,7 +225,8 @@ __global__ void k_particle_keys(const float* __restrict__ ps, int64_t stride, in
 }
 
 __global__ void k_ranges(const uint32_t* __restrict__ skey, int64_t n, int shift, int64_t nblocks,
-                         int* __restrict__ bstart, int* __restrict__ bend, int* __restrict__ pblocks, DevStatus* st) {
+                         int* __restrict__ bstart, int* __restrict__ bend, int* __restrict__ pblocks,
+                         int* __restrict__ hasp, int gen, DevStatus* st) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const uint32_t r = skey[i] >> shift;
@@ -223,22 +238,60 @@ __global__ void k_ranges(const uint32_t* __restrict__ skey, int64_t n, int shift
     const bool last = (i == n - 1) || ((skey[i + 1] >> shift) != r);
     if (first) {
         bstart[r] = (int)i;
+        hasp[r] = gen;
         pblocks[atomicAdd(&st->n_pblocks, 1u)] = (int)r;
     }
     if (last) bend[r] = (int)(i + 1);
 }
 
-// cellstart[q] = first sorted position with key >= q (binary search).
-__global__ void k_cellstart(const uint32_t* __restrict__ skey, int64_t n, int64_t ncells, int* __restrict__ cs) {
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q > ncells) return;
-    int64_t lo = 0, hi = n;
+__device__ __forceinline__ int first_geq(const uint32_t* __restrict__ skey, int lo, int hi, uint32_t q) {
     while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if ((int64_t)skey[mid] < q) lo = mid + 1;
+        const int mid = (lo + hi) >> 1;
+        if (skey[mid] < q) lo = mid + 1;
         else hi = mid;
     }
-    cs[q] = (int)lo;
+    return lo;
+}
+
+// Reorders every block's particles from (cell, k) to k-major order: the
+// k-th particle of each cell (cells in l order) before any (k+1)-th one, and
+// records the particle count per cell.  One warp per block; lane l handles
+// cells l and l + 32.  Output goes to the spare sort buffers.
+__global__ void __launch_bounds__(128) k_interleave(const uint32_t* __restrict__ skey, const uint32_t* __restrict__ perm,
+                                                    const int* __restrict__ bstart, const int* __restrict__ bend,
+                                                    const int* __restrict__ pblocks, const DevStatus* __restrict__ stc,
+                                                    uint32_t* __restrict__ skey2, uint32_t* __restrict__ perm2,
+                                                    int* __restrict__ ccount) {
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * 4 + (threadIdx.x >> 5), nw = gridDim.x * 4;
+    const unsigned FULL = 0xffffffffu, lt = (1u << lane) - 1u;
+    const int nblk = (int)stc->n_pblocks;
+    for (int kb = gw; kb < nblk; kb += nw) {
+        const int r = pblocks[kb];
+        const int s = bstart[r], e = bend[r];
+        const uint32_t base = (uint32_t)r * 64u;
+        const int lo0 = first_geq(skey, s, e, base + lane), hi0 = first_geq(skey, lo0, e, base + lane + 1);
+        const int lo1 = first_geq(skey, s, e, base + 32 + lane), hi1 = first_geq(skey, lo1, e, base + 33 + lane);
+        const int cnt0 = hi0 - lo0, cnt1 = hi1 - lo1;
+        ccount[(int64_t)r * 64 + lane] = cnt0;
+        ccount[(int64_t)r * 64 + 32 + lane] = cnt1;
+        int off = 0;
+        for (int k = 0; k <= e - s; ++k) {   // no cell holds more than the block's particles
+            const unsigned M0 = __ballot_sync(FULL, cnt0 > k), M1 = __ballot_sync(FULL, cnt1 > k);
+            if ((M0 | M1) == 0u) break;
+            if (cnt0 > k) {
+                const int pos = s + off + __popc(M0 & lt);
+                perm2[pos] = perm[lo0 + k];
+                skey2[pos] = base + lane;
+            }
+            if (cnt1 > k) {
+                const int pos = s + off + __popc(M0) + __popc(M1 & lt);
+                perm2[pos] = perm[lo1 + k];
+                skey2[pos] = base + 32 + lane;
+            }
+            off += __popc(M0) + __popc(M1);
+        }
+    }
 }
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -283,7 +336,13 @@ cudaError_t launch_assign(mpm_ctx* c) {
     int sel = radix_sort_pairs(c, c->akey, c->aslot, c->n_active, nullptr, bits, c->st);
     k_assign<<<blocks_for(c->n_active * c->B3, 256), 256, 0, c->st>>>(c->akey[sel], c->aslot[sel], c->n_active, c->P,
                                                                       c->hvals, c->bcoord, c->gmv, c->gf, c->B3, zero);
-    ++c->launches;
+    HashView hv{c->hkeys, c->hvals, (uint64_t)(c->H - 1)};
+    const int nnb = c->B == 4 ? 8 : 27;
+    if (c->B == 4)
+        k_neighbours<4><<<blocks_for(c->n_active * nnb, 256), 256, 0, c->st>>>(c->bcoord, c->n_active, c->P, hv, c->nbr);
+    else
+        k_neighbours<1><<<blocks_for(c->n_active * nnb, 256), 256, 0, c->st>>>(c->bcoord, c->n_active, c->P, hv, c->nbr);
+    c->launches += 2;
     return cudaGetLastError();
 }
 
@@ -308,11 +367,13 @@ cudaError_t launch_particle_keys(mpm_ctx* c) {
 cudaError_t launch_ranges(mpm_ctx* c, const uint32_t* skey) {
     const int shift = (c->B == 4) ? 6 : 0;
     k_ranges<<<blocks_for(c->n, 256), 256, 0, c->st>>>(skey, c->n, shift, c->n_active, c->bstart, c->bend, c->pblocks,
-                                                        c->dstat);
+                                                        c->hasp, c->gen, c->dstat);
     ++c->launches;
-    if (c->det) {
-        const int64_t ncells = c->n_active * c->B3;
-        k_cellstart<<<blocks_for(ncells + 1, 256), 256, 0, c->st>>>(skey, c->n, ncells, c->cellstart);
+    if (c->B == 4) {
+        const int o = 1 - c->sorted_sel;
+        k_interleave<<<148 * 8, 128, 0, c->st>>>(skey, c->pval[c->sorted_sel], c->bstart, c->bend, c->pblocks, c->dstat,
+                                                c->pkey[o], c->pval[o], c->ccount);
+        c->sorted_sel = o;
         ++c->launches;
     }
     return cudaGetLastError();

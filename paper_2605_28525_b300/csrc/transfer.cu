@@ -11,17 +11,16 @@
 //      which also stores the Kirchhoff stress tau for the next P2G.
 //
 // Two P2G variants:
-//   k_p2g_tile    one CTA per block that holds particles.  The block's
-//                 particles (sorted by cell) are staged in shared memory; work
-//                 item (x-offset a, cell) sums the cell's particles into the 9
-//                 nodes (a, 0..2, 0..2) in registers, then adds them to a
-//                 (B+2)^3 shared tile; the tile is flushed with float4 global
-//                 atomics into the active nodes of the block and its +1
-//                 neighbours.  Fast; summation order varies between runs.
-//   k_p2g_gather  one thread per active node; sums the particles of its 27
-//                 neighbouring cells in a fixed order (cell offset, then
-//                 sorted particle order = (block, cell, id)).  Deterministic,
-//                 and bit-identical between the sparse and the dense grid.
+//   k_p2g_cells   one warp per block that holds particles, lane = cell, with
+//                 the block's particles in k-major order; register sums per
+//                 (cell, x-offset) and a warp-private shared tile updated
+//                 without atomics, flushed with float4 global atomics into the
+//                 active nodes.  Fast; the order of the global adds varies.
+//   deterministic the same kernel with the block's particles in (cell, id)
+//                 order; each block stores its tile and k_p2g_reduce sums
+//                 the <= 8 tiles of every node in a fixed order: results are
+//                 bit-identical between runs and between sparse and dense.
+//   k_p2g_atomic  the node-level (B = 1) set: per-particle float4 atomics.
 #include <algorithm>
 
 #include "mpm_internal.cuh"
@@ -57,89 +56,54 @@ __device__ __forceinline__ int block_rank(const Params& P, const HashView& hv, i
     return hash_find(hv, pack_key(bi, bj, bk), P.max_probe);
 }
 
-__device__ __forceinline__ int first_geq(const uint32_t* __restrict__ skey, int lo, int hi, uint32_t q) {
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if (skey[mid] < q) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
+// ------------------------------------------------------- P2G: cell lanes
 
-// ------------------------------------------------------- P2G: block tile
-
-template <int B>
-struct TileCfg {
-    static constexpr int T = B + 2;                 // tile edge in nodes
-    static constexpr int NC = B * B * B;            // cells per block
-    static constexpr int NI = 3 * NC;               // (a, cell) work items
-    static constexpr int NT = (B == 4) ? 192 : 32;  // threads per CTA
-    static constexpr int CH = (B == 4) ? 384 : 64;  // particles staged at once
-    static constexpr int CHP = CH + CH / 8;         // padded stride (bank swizzle)
-    static constexpr int SY = (B == 4) ? 8 : 3;     // tile strides (conflict-free for
-    static constexpr int SZ = (B == 4) ? 68 : 9;    // 32 consecutive cells)
+// Particles of a block are stored "k-major": the k-th particle of every cell
+// (cells in l order) before the (k+1)-th particle of any cell; ccount holds
+// the particles per cell.  One warp owns one block and a private tile of
+// (B+2)^3 = 216 nodes; lane l owns cell h*32 + l of half h (cz in {2h, 2h+1}).
+// For each (half, x-offset a) pass the lanes walk k = 0, 1, ...: the k-th
+// particles of the 32 cells are consecutive in memory (coalesced loads), and
+// each lane accumulates its particle's 9 nodes (a, 0..2, 0..2) x 7 channels
+// in registers.  At the end of a pass the lanes hold distinct cells and the
+// same a, so for each node offset (b, c) their target nodes are distinct:
+// the tile is updated with plain read-modify-write, one warp-synchronised
+// step per offset, no atomics.  The finished tile is added to the active
+// nodes with float4 global atomics.
+struct CellTileCfg {
+    static constexpr int T = 6;                    // tile edge (B + 2 with B = 4)
+    static constexpr int SY = 8, SZ = 68;          // strides: conflict-free for one half's 32 cells
     static constexpr int TILE = (T - 1) * (SZ + SY) + T;
-    static constexpr int R = (B == 4) ? 2 : 3;      // neighbour blocks per axis
-    static constexpr int NNB = R * R * R;
+    static constexpr int WARPS = 4;
 };
 
-__device__ __forceinline__ int swz(int t) { return t + (t >> 3); }
-
-template <int B, bool DENSE>
-__global__ void __launch_bounds__(TileCfg<B>::NT) k_p2g_tile(
-    const float* __restrict__ ps, int64_t stride, const uint32_t* __restrict__ skey,
-    const uint32_t* __restrict__ perm, const int* __restrict__ bstart, const int* __restrict__ bend,
-    const int* __restrict__ pblocks, const DevStatus* __restrict__ stc, Params P, HashView hv,
-    const int4* __restrict__ bcoord, float4* __restrict__ gmv, float4* __restrict__ gf, DevStatus* st) {
-    using K = TileCfg<B>;
-    __shared__ float s_d[3][K::CHP];
-    __shared__ float s_v[3][K::CHP];
-    __shared__ float s_c[9][K::CHP];
-    __shared__ float s_t[6][K::CHP];
-    __shared__ float s_tile[7][K::TILE];
-    __shared__ int s_cs[K::NC + 1];
-    __shared__ int s_nb[K::NNB];
-    const int tid = threadIdx.x;
+template <bool DENSE, bool DET>
+__global__ void __launch_bounds__(CellTileCfg::WARPS * 32, 4) k_p2g_cells(
+    const float* __restrict__ ps, int64_t stride, const uint32_t* __restrict__ perm,
+    const int* __restrict__ bstart, const int* __restrict__ bend, const int* __restrict__ pblocks,
+    const int* __restrict__ ccount, const DevStatus* __restrict__ stc, Params P, const int* __restrict__ nbr,
+    float4* __restrict__ gmv, float4* __restrict__ gf, float* __restrict__ tbuf, DevStatus* st) {
+    using K = CellTileCfg;
+    __shared__ float tiles[K::WARPS][7][K::TILE];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float(&tile)[7][K::TILE] = tiles[wid];
     const int nblk = (int)stc->n_pblocks;
+    const int gw = blockIdx.x * K::WARPS + wid, nw = gridDim.x * K::WARPS;
+    const unsigned FULL = 0xffffffffu, lt = (1u << lane) - 1u;
 
-    for (int i = tid; i < 7 * K::TILE; i += K::NT) (&s_tile[0][0])[i] = 0.f;
+    for (int i = lane; i < 7 * K::TILE; i += 32) (&tile[0][0])[i] = 0.f;
+    __syncwarp();
 
-    for (int kb = blockIdx.x; kb < nblk; kb += gridDim.x) {
+    for (int kb = gw; kb < nblk; kb += nw) {
         const int r = pblocks[kb];
-        const int s = bstart[r], e = bend[r];
-        int bc[3];
-        block_coords<DENSE>(P, bcoord, r, bc);
-        if (tid < K::NNB) {
-            const int jx = tid / (K::R * K::R), jy = (tid / K::R) % K::R, jz = tid % K::R;
-            s_nb[tid] = block_rank<DENSE>(P, hv, bc[0] + jx, bc[1] + jy, bc[2] + jz);
-        }
-        for (int c = tid; c <= K::NC; c += K::NT)
-            s_cs[c] = first_geq(skey, s, e, (uint32_t)r * K::NC + (uint32_t)c) - s;
-        __syncthreads();
-
-        const int np = e - s;
-        for (int c0 = 0; c0 < np; c0 += K::CH) {
-            const int cn = min(K::CH, np - c0);
-            for (int t = tid; t < cn; t += K::NT) {
-                const int64_t p = perm[s + c0 + t];
-                const int q = swz(t);
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    const float fx = ps[(PX + a) * stride + p] * P.inv_h;
-                    s_d[a][q] = fx - (float)base_index(fx);    // exact
-                    s_v[a][q] = ps[(PV + a) * stride + p];
-                }
-#pragma unroll
-                for (int a = 0; a < 9; ++a) s_c[a][q] = ps[(PC + a) * stride + p] * P.h;
-#pragma unroll
-                for (int a = 0; a < 6; ++a) s_t[a][q] = ps[(PT + a) * stride + p];
-            }
-            __syncthreads();
-            for (int it = tid; it < K::NI; it += K::NT) {
-                const int a = it / K::NC, cell = it % K::NC;
-                const int cx = cell % B, cy = (cell / B) % B, cz = cell / (B * B);
-                const int lo = max(s_cs[cell], c0), hi = min(s_cs[cell + 1], c0 + cn);
-                if (lo >= hi) continue;
+        const int s = bstart[r], kcap = bend[r] - s;   // no cell holds more than the block's particles
+        const int cnt0 = ccount[(int64_t)r * 64 + lane], cnt1 = ccount[(int64_t)r * 64 + 32 + lane];
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            const int cnt = h ? cnt1 : cnt0;
+            const int cx = lane & 3, cy = (lane >> 2) & 3, cz = 2 * h + (lane >> 4);
+#pragma unroll 1
+            for (int a = 0; a < 3; ++a) {
                 float acc[3][3][7];
 #pragma unroll
                 for (int b = 0; b < 3; ++b)
@@ -147,140 +111,206 @@ __global__ void __launch_bounds__(TileCfg<B>::NT) k_p2g_tile(
                     for (int cc = 0; cc < 3; ++cc)
 #pragma unroll
                         for (int k = 0; k < 7; ++k) acc[b][cc][k] = 0.f;
-                for (int j = lo; j < hi; ++j) {
-                    const int q = swz(j - c0);
-                    const float dx = s_d[0][q], dy = s_d[1][q], dz = s_d[2][q];
-                    float wx, dwx, wy[3], dwy[3], wz[3], dwz[3];
-                    bspline_a(dx, a, wx, dwx);
-                    bspline3(dy, wy, dwy);
-                    bspline3(dz, wz, dwz);
-                    const float ox = (float)a - dx;
-                    float hc[9];
+                int off = 0;
+                for (int k = 0;; ++k) {
+                    const unsigned M0 = __ballot_sync(FULL, cnt0 > k), M1 = __ballot_sync(FULL, cnt1 > k);
+                    if ((M0 | M1) == 0u) break;
+                    if (k >= kcap || off + __popc(M0) + __popc(M1) > kcap) {   // inconsistent counts
+                        if (lane == 0) atomicOr(&st->map_miss, 2u);
+                        break;
+                    }
+                    if (cnt > k) {
+                        const int idx = h ? __popc(M0) + __popc(M1 & lt) : __popc(M0 & lt);
+                        const int64_t p = perm[s + off + idx];
+                        float d[3], v[3], hc[9], t[6];
 #pragma unroll
-                    for (int k = 0; k < 9; ++k) hc[k] = s_c[k][q];
-                    const float t00 = s_t[0][q], t01 = s_t[1][q], t02 = s_t[2][q];
-                    const float t11 = s_t[3][q], t12 = s_t[4][q], t22 = s_t[5][q];
-                    const float q0x = fmaf(hc[0], ox, s_v[0][q]);
-                    const float q0y = fmaf(hc[3], ox, s_v[1][q]);
-                    const float q0z = fmaf(hc[6], ox, s_v[2][q]);
+                        for (int q = 0; q < 3; ++q) {
+                            const float fx = ps[(PX + q) * stride + p] * P.inv_h;
+                            d[q] = fx - (float)base_index(fx);      // exact
+                            v[q] = ps[(PV + q) * stride + p];
+                        }
 #pragma unroll
-                    for (int b = 0; b < 3; ++b) {
-                        const float oy = (float)b - dy;
-                        const float qbx = fmaf(hc[1], oy, q0x), qby = fmaf(hc[4], oy, q0y), qbz = fmaf(hc[7], oy, q0z);
+                        for (int q = 0; q < 9; ++q) hc[q] = ps[(PC + q) * stride + p] * P.h;
 #pragma unroll
-                        for (int cc = 0; cc < 3; ++cc) {
-                            const float oz = (float)cc - dz;
-                            const float wyz = wy[b] * wz[cc];
-                            const float N = wx * wyz;
-                            const float gx = dwx * wyz, gy = wx * dwy[b] * wz[cc], gz = wx * wy[b] * dwz[cc];
-                            const float mx = fmaf(hc[2], oz, qbx), my = fmaf(hc[5], oz, qby), mz = fmaf(hc[8], oz, qbz);
-                            acc[b][cc][0] += N;
-                            acc[b][cc][1] = fmaf(N, mx, acc[b][cc][1]);
-                            acc[b][cc][2] = fmaf(N, my, acc[b][cc][2]);
-                            acc[b][cc][3] = fmaf(N, mz, acc[b][cc][3]);
-                            acc[b][cc][4] += gx * t00 + gy * t01 + gz * t02;
-                            acc[b][cc][5] += gx * t01 + gy * t11 + gz * t12;
-                            acc[b][cc][6] += gx * t02 + gy * t12 + gz * t22;
+                        for (int q = 0; q < 6; ++q) t[q] = ps[(PT + q) * stride + p];
+                        float wx, dwx, wy[3], dwy[3], wz[3], dwz[3];
+                        bspline_a(d[0], a, wx, dwx);
+                        bspline3(d[1], wy, dwy);
+                        bspline3(d[2], wz, dwz);
+                        // momentum at node (a, b, c): v + hC (a - dx, b - dy, c - dz)
+                        const float ox = (float)a - d[0];
+                        const float q0x = fmaf(hc[0], ox, v[0]) - hc[1] * d[1] - hc[2] * d[2];
+                        const float q0y = fmaf(hc[3], ox, v[1]) - hc[4] * d[1] - hc[5] * d[2];
+                        const float q0z = fmaf(hc[6], ox, v[2]) - hc[7] * d[1] - hc[8] * d[2];
+#pragma unroll
+                        for (int b = 0; b < 3; ++b) {
+                            // tau . grad N over c: wz (tau_r0 dwx wy + tau_r1 wx dwy) + dwz tau_r2 wx wy
+                            const float Pw = wx * wy[b], Gx = dwx * wy[b], Gy = wx * dwy[b];
+                            const float A0 = t[0] * Gx + t[1] * Gy, A1 = t[1] * Gx + t[3] * Gy,
+                                        A2 = t[2] * Gx + t[4] * Gy;
+                            const float B0 = t[2] * Pw, B1 = t[4] * Pw, B2 = t[5] * Pw;
+                            const float qbx = fmaf(hc[1], (float)b, q0x), qby = fmaf(hc[4], (float)b, q0y),
+                                        qbz = fmaf(hc[7], (float)b, q0z);
+#pragma unroll
+                            for (int cc = 0; cc < 3; ++cc) {
+                                const float N = Pw * wz[cc];
+                                const float mx = fmaf(hc[2], (float)cc, qbx), my = fmaf(hc[5], (float)cc, qby),
+                                            mz = fmaf(hc[8], (float)cc, qbz);
+                                acc[b][cc][0] += N;
+                                acc[b][cc][1] = fmaf(N, mx, acc[b][cc][1]);
+                                acc[b][cc][2] = fmaf(N, my, acc[b][cc][2]);
+                                acc[b][cc][3] = fmaf(N, mz, acc[b][cc][3]);
+                                acc[b][cc][4] = fmaf(wz[cc], A0, fmaf(dwz[cc], B0, acc[b][cc][4]));
+                                acc[b][cc][5] = fmaf(wz[cc], A1, fmaf(dwz[cc], B1, acc[b][cc][5]));
+                                acc[b][cc][6] = fmaf(wz[cc], A2, fmaf(dwz[cc], B2, acc[b][cc][6]));
+                            }
                         }
                     }
+                    off += __popc(M0) + __popc(M1);
                 }
+                // For one node offset (b, c) the lanes' targets are distinct, but
+                // lane A's (b, c+1) target is lane B's (b, c) target when B's cell
+                // is one above A's: each offset is a separate warp-ordered step.
 #pragma unroll
                 for (int b = 0; b < 3; ++b)
 #pragma unroll
                     for (int cc = 0; cc < 3; ++cc) {
-                        const int ti = (cx + a) + K::SY * (cy + b) + K::SZ * (cz + cc);
+                        if (cnt > 0) {
+                            const int ti = (cx + a) + K::SY * (cy + b) + K::SZ * (cz + cc);
 #pragma unroll
-                        for (int k = 0; k < 7; ++k) atomicAdd(&s_tile[k][ti], acc[b][cc][k]);
+                            for (int k = 0; k < 7; ++k) tile[k][ti] += acc[b][cc][k];
+                        }
+                        __syncwarp();
                     }
             }
-            __syncthreads();
         }
-
-        // flush the tile into the active nodes of this block and its neighbours
+        // flush the tile: deterministic mode stores it for k_p2g_reduce, the
+        // fast mode adds it to the active nodes of this block and its neighbours
         const float fs = -P.V0 * P.inv_h;
-        for (int t = tid; t < K::T * K::T * K::T; t += K::NT) {
+        for (int t = lane; t < K::T * K::T * K::T; t += 32) {
             const int tx = t % K::T, ty = (t / K::T) % K::T, tz = t / (K::T * K::T);
             const int ti = tx + K::SY * ty + K::SZ * tz;
             float v[7];
 #pragma unroll
             for (int k = 0; k < 7; ++k) {
-                v[k] = s_tile[k][ti];
-                s_tile[k][ti] = 0.f;
+                v[k] = tile[k][ti];
+                tile[k][ti] = 0.f;
+            }
+            if (DET) {
+                float* T = tbuf + (int64_t)r * (7 * 216);
+#pragma unroll
+                for (int k = 0; k < 7; ++k) T[k * 216 + t] = v[k];
+                continue;
             }
             if (v[0] == 0.f && v[1] == 0.f && v[2] == 0.f && v[3] == 0.f && v[4] == 0.f && v[5] == 0.f &&
                 v[6] == 0.f)
                 continue;
-            const int nbx = tx / B, nby = ty / B, nbz = tz / B;
-            const int rank = s_nb[(nbx * K::R + nby) * K::R + nbz];
+            const int ex = tx >> 2, ey = ty >> 2, ez = tz >> 2;
+            int rank;
+            if (DENSE) rank = r + (ex * P.nb[1] + ey) * P.nb[2] + ez;
+            else rank = __ldg(&nbr[(int64_t)r * 8 + (ex * 2 + ey) * 2 + ez]);
             if (rank < 0) {
                 atomicOr(&st->map_miss, 1u);
                 continue;
             }
-            const int l = (tx % B) + B * ((ty % B) + B * (tz % B));
-            const int64_t g = (int64_t)rank * K::NC + l;
+            const int l = (tx & 3) + 4 * ((ty & 3) + 4 * (tz & 3));
+            const int64_t g = (int64_t)rank * 64 + l;
             atomicAdd(&gmv[g], make_float4(v[0] * P.mp, v[1] * P.mp, v[2] * P.mp, v[3] * P.mp));
             atomicAdd(&gf[g], make_float4(v[4] * fs, v[5] * fs, v[6] * fs, 0.f));
         }
-        __syncthreads();
+        __syncwarp();
     }
 }
 
-// ----------------------------------------------------- P2G: fixed order
+// --------------------------------------------- P2G: deterministic reduce
 
-template <int B, bool DENSE>
-__global__ void __launch_bounds__(128) k_p2g_gather(
-    const float* __restrict__ ps, int64_t stride, const uint32_t* __restrict__ perm,
-    const int* __restrict__ cellstart, int64_t nnodes, Params P, HashView hv, const int4* __restrict__ bcoord,
-    float4* __restrict__ gmv, float4* __restrict__ gf) {
-    constexpr int S = (B == 4) ? 2 : 0;
-    constexpr int NC = B * B * B;
+// Deterministic mode: every block writes its finished tile (7 channels x
+// 216 nodes) to tbuf instead of adding it to the grid.  Each active node then
+// sums the tiles of the (at most 8) blocks b - e, e in {0,1}^3, that cover it,
+// in the fixed order e = 0..7 and only for blocks that hold particles this
+// step.  The result does not depend on thread timing, and the sparse and the
+// dense grid produce the same bits (absent blocks hold no particles).
+template <bool DENSE>
+__global__ void __launch_bounds__(256) k_p2g_reduce(int64_t nnodes, Params P, HashView hv,
+                                                    const int4* __restrict__ bcoord, const float* __restrict__ tbuf,
+                                                    const int* __restrict__ hasp, int gen, float4* __restrict__ gmv,
+                                                    float4* __restrict__ gf) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nnodes) return;
-    const int r = (int)(i / NC), l = (int)(i % NC);
+    const int r = (int)(i >> 6), l = (int)(i & 63);
+    const int lx = l & 3, ly = (l >> 2) & 3, lz = l >> 4;
     int bc[3];
     block_coords<DENSE>(P, bcoord, r, bc);
-    const int n[3] = {bc[0] * B + l % B, bc[1] * B + (l / B) % B, bc[2] * B + l / (B * B)};
-    float m = 0.f, mvx = 0.f, mvy = 0.f, mvz = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b)
-            for (int c = 0; c < 3; ++c) {
-                const int ci = n[0] - a, cj = n[1] - b, ck = n[2] - c;   // cell whose stencil holds n at (a,b,c)
-                const int rank = block_rank<DENSE>(P, hv, ci >> S, cj >> S, ck >> S);
-                if (rank < 0) continue;
-                const int lc = (ci & (B - 1)) + B * ((cj & (B - 1)) + B * (ck & (B - 1)));
-                const int q = rank * NC + lc;
-                const int lo = cellstart[q], hi = cellstart[q + 1];
-                for (int j = lo; j < hi; ++j) {
-                    const int64_t p = perm[j];
-                    const float dx = ps[(PX + 0) * stride + p] * P.inv_h - (float)ci;
-                    const float dy = ps[(PX + 1) * stride + p] * P.inv_h - (float)cj;
-                    const float dz = ps[(PX + 2) * stride + p] * P.inv_h - (float)ck;
-                    float wx, dwx, wy, dwy, wz, dwz;
-                    bspline_a(dx, a, wx, dwx);
-                    bspline_a(dy, b, wy, dwy);
-                    bspline_a(dz, c, wz, dwz);
-                    const float N = wx * wy * wz;
-                    const float gx = dwx * wy * wz, gy = wx * dwy * wz, gz = wx * wy * dwz;
-                    const float ox = ((float)a - dx) * P.h, oy = ((float)b - dy) * P.h, oz = ((float)c - dz) * P.h;
-                    const float* Cp = ps + PC * stride + p;
-                    const float mx = ps[(PV + 0) * stride + p] + Cp[0] * ox + Cp[1 * stride] * oy + Cp[2 * stride] * oz;
-                    const float my = ps[(PV + 1) * stride + p] + Cp[3 * stride] * ox + Cp[4 * stride] * oy + Cp[5 * stride] * oz;
-                    const float mz = ps[(PV + 2) * stride + p] + Cp[6 * stride] * ox + Cp[7 * stride] * oy + Cp[8 * stride] * oz;
-                    const float t00 = ps[(PT + 0) * stride + p], t01 = ps[(PT + 1) * stride + p];
-                    const float t02 = ps[(PT + 2) * stride + p], t11 = ps[(PT + 3) * stride + p];
-                    const float t12 = ps[(PT + 4) * stride + p], t22 = ps[(PT + 5) * stride + p];
-                    m += N;
-                    mvx += N * mx;
-                    mvy += N * my;
-                    mvz += N * mz;
-                    g0 += gx * t00 + gy * t01 + gz * t02;
-                    g1 += gx * t01 + gy * t11 + gz * t12;
-                    g2 += gx * t02 + gy * t12 + gz * t22;
-                }
-            }
+    float v[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const int ex = e >> 2, ey = (e >> 1) & 1, ez = e & 1;
+        if ((ex && lx > 1) || (ey && ly > 1) || (ez && lz > 1)) continue;   // outside that block's tile
+        const int rs = block_rank<DENSE>(P, hv, bc[0] - ex, bc[1] - ey, bc[2] - ez);
+        if (rs < 0 || hasp[rs] != gen) continue;
+        const int t = (lx + 4 * ex) + 6 * ((ly + 4 * ey) + 6 * (lz + 4 * ez));
+        const float* T = tbuf + (int64_t)rs * (7 * 216);
+#pragma unroll
+        for (int k = 0; k < 7; ++k) v[k] += T[k * 216 + t];
+    }
     const float fs = -P.V0 * P.inv_h;
-    gmv[i] = make_float4(m * P.mp, mvx * P.mp, mvy * P.mp, mvz * P.mp);
-    gf[i] = make_float4(g0 * fs, g1 * fs, g2 * fs, 0.f);
+    gmv[i] = make_float4(v[0] * P.mp, v[1] * P.mp, v[2] * P.mp, v[3] * P.mp);
+    gf[i] = make_float4(v[4] * fs, v[5] * fs, v[6] * fs, 0.f);
+}
+
+// --------------------------------------------------- P2G: node-level sets
+
+// B = 1 (every node its own block): one thread per particle, the 27 node
+// contributions added with float4 global atomics into the nodes found
+// through the particle's neighbour table.  A validation mode for the
+// node-level active set; the grid was zeroed by the rebuild.
+__global__ void __launch_bounds__(256) k_p2g_atomic(const float* __restrict__ ps, int64_t stride,
+                                                    const uint32_t* __restrict__ perm,
+                                                    const uint32_t* __restrict__ skey, int64_t n,
+                                                    const int* __restrict__ nbr, Params P, float4* __restrict__ gmv,
+                                                    float4* __restrict__ gf, DevStatus* st) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t p = perm[i];
+    const int r = (int)skey[i];
+    float d[3], v[3], hc[9], t[6];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const float fx = ps[(PX + q) * stride + p] * P.inv_h;
+        d[q] = fx - (float)base_index(fx);
+        v[q] = ps[(PV + q) * stride + p];
+    }
+#pragma unroll
+    for (int q = 0; q < 9; ++q) hc[q] = ps[(PC + q) * stride + p] * P.h;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) t[q] = ps[(PT + q) * stride + p];
+    float wx[3], dwx[3], wy[3], dwy[3], wz[3], dwz[3];
+    bspline3(d[0], wx, dwx);
+    bspline3(d[1], wy, dwy);
+    bspline3(d[2], wz, dwz);
+    const float fs = -P.V0 * P.inv_h;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int rank = __ldg(&nbr[(int64_t)r * 27 + (a * 3 + b) * 3 + c]);
+                if (rank < 0) {
+                    atomicOr(&st->map_miss, 1u);
+                    continue;
+                }
+                const float N = wx[a] * wy[b] * wz[c];
+                const float gx = dwx[a] * wy[b] * wz[c], gy = wx[a] * dwy[b] * wz[c], gz = wx[a] * wy[b] * dwz[c];
+                const float ox = (float)a - d[0], oy = (float)b - d[1], oz = (float)c - d[2];
+                const float mx = v[0] + hc[0] * ox + hc[1] * oy + hc[2] * oz;
+                const float my = v[1] + hc[3] * ox + hc[4] * oy + hc[5] * oz;
+                const float mz = v[2] + hc[6] * ox + hc[7] * oy + hc[8] * oz;
+                atomicAdd(&gmv[rank], make_float4(N * P.mp, N * mx * P.mp, N * my * P.mp, N * mz * P.mp));
+                atomicAdd(&gf[rank], make_float4((gx * t[0] + gy * t[1] + gz * t[2]) * fs,
+                                                 (gx * t[1] + gy * t[3] + gz * t[4]) * fs,
+                                                 (gx * t[2] + gy * t[4] + gz * t[5]) * fs, 0.f));
+            }
 }
 
 // ------------------------------------------------------------ grid update
@@ -383,14 +413,25 @@ __device__ __forceinline__ bool nh_tau(const Params& P, const float F[9], Sym& t
     return true;
 }
 
+#ifndef MPM_SVD_SWEEPS
+#define MPM_SVD_SWEEPS 4
+#endif
+
 // One Jacobi rotation of the symmetric S in the (p, q) plane, accumulated in
-// V (columns).  Standard cyclic Jacobi for symmetric eigenproblems.
+// V (columns).  The tangent of the rotation angle is the smaller root of
+// t^2 + 2 theta t - 1 = 0 with theta = (S_qq - S_pp) / (2 S_pq), written as
+// t = 2 S_pq sign(d) / (|d| + sqrt(d^2 + 4 S_pq^2)), d = S_qq - S_pp, which
+// needs no division by S_pq.  Couplings below 1e-12 of the diagonal are
+// treated as converged.
 template <int p, int q, int r>
 __device__ __forceinline__ void jacobi_rot(float S[3][3], float V[3][3]) {
     const float spq = S[p][q];
-    if (spq == 0.f) return;
-    const float theta = (S[q][q] - S[p][p]) / (2.f * spq);
-    const float t = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.f)));
+    // negligible coupling: no rotation (this also keeps the division below
+    // away from denormal operands once the sweeps have converged)
+    if (!(fabsf(spq) > 1e-12f * (fabsf(S[p][p]) + fabsf(S[q][q])))) return;
+    const float dd = S[q][q] - S[p][p];
+    const float den = fabsf(dd) + sqrtf(fmaf(dd, dd, 4.f * spq * spq));
+    const float t = copysignf(2.f, dd) * __fdividef(spq, den);
     const float c = rsqrtf(fmaf(t, t, 1.f));
     const float s = t * c;
     S[p][p] -= t * spq;
@@ -420,7 +461,7 @@ __device__ __forceinline__ bool svd3(const float F[9], float U[3][3], float sig[
             V[i][j] = (i == j) ? 1.f : 0.f;
         }
 #pragma unroll
-    for (int sweep = 0; sweep < 5; ++sweep) {
+    for (int sweep = 0; sweep < MPM_SVD_SWEEPS; ++sweep) {
         jacobi_rot<0, 1, 2>(S, V);
         jacobi_rot<0, 2, 1>(S, V);
         jacobi_rot<1, 2, 0>(S, V);
@@ -538,147 +579,168 @@ __device__ __forceinline__ bool hencky_tau(const Params& P, const float F[9], Sy
 
 // ------------------------------------------------------------------- G2P
 
+// Compact index of the neighbour block e = (ex, ey, ez) (each 0..R-1) of
+// block r: the per-block table (sparse) or the box arithmetic (dense).
+template <int B, bool DENSE>
+struct Neighbours {
+    static constexpr int R = (B == 4) ? 2 : 3;
+    static constexpr int NNB = R * R * R;
+    int q[NNB];
+    __device__ __forceinline__ void load(const Params& P, const int* __restrict__ nbr, int r) {
+        if (DENSE) {
+            const int sx = P.nb[1] * P.nb[2], sy = P.nb[2];
+#pragma unroll
+            for (int e = 0; e < NNB; ++e) q[e] = r + (e / (R * R)) * sx + ((e / R) % R) * sy + (e % R);
+        } else {
+            if (B == 4) {
+                const int4 a = __ldg(reinterpret_cast<const int4*>(nbr) + 2 * r);
+                const int4 b = __ldg(reinterpret_cast<const int4*>(nbr) + 2 * r + 1);
+                q[0] = a.x; q[1] = a.y; q[2] = a.z; q[3] = a.w;
+                q[4] = b.x; q[5] = b.y; q[6] = b.z; q[7] = b.w;
+            } else {
+#pragma unroll
+                for (int e = 0; e < NNB; ++e) q[e] = __ldg(&nbr[(int64_t)r * NNB + e]);
+            }
+        }
+    }
+};
+
+// G2P: one thread per particle in sorted order, no shared memory and no
+// barriers.  The 27 node velocities come from the grid through the
+// neighbour table (L1-resident for the particles of one block).  The node
+// sums are factored over z: for each (a, b) the three z-nodes are first
+// reduced with w_z, dw_z and c w_z, then scattered into v_p, B_p and L_p.
 template <int B, bool DENSE, int MAT>
 __global__ void __launch_bounds__(256) k_g2p(const float* __restrict__ ps, float* __restrict__ po, int64_t stride,
-                                              const uint32_t* __restrict__ perm, const int* __restrict__ bstart,
-                                              const int* __restrict__ bend, const int* __restrict__ pblocks,
-                                              const DevStatus* __restrict__ stc, Params P, HashView hv,
-                                              const int4* __restrict__ bcoord, const float4* __restrict__ gv,
-                                              DevStatus* st) {
-    constexpr int T = B + 2;
+                                              const uint32_t* __restrict__ perm, const uint32_t* __restrict__ skey,
+                                              int64_t n, const int* __restrict__ nbr, Params P,
+                                              const float4* __restrict__ gv, DevStatus* st) {
+    constexpr int S3 = (B == 4) ? 6 : 0;
     constexpr int NC = B * B * B;
-    constexpr int R = (B == 4) ? 2 : 3;
-    __shared__ float4 s_v[T * T * T];
-    __shared__ int s_nb[R * R * R];
-    const int tid = threadIdx.x;
-    const int nblk = (int)stc->n_pblocks;
-    for (int kb = blockIdx.x; kb < nblk; kb += gridDim.x) {
-        const int r = pblocks[kb];
-        const int s = bstart[r], e = bend[r];
-        int bc[3];
-        block_coords<DENSE>(P, bcoord, r, bc);
-        if (tid < R * R * R) {
-            const int jx = tid / (R * R), jy = (tid / R) % R, jz = tid % R;
-            s_nb[tid] = block_rank<DENSE>(P, hv, bc[0] + jx, bc[1] + jy, bc[2] + jz);
-        }
-        __syncthreads();
-        for (int t = tid; t < T * T * T; t += blockDim.x) {
-            const int tx = t % T, ty = (t / T) % T, tz = t / (T * T);
-            const int rank = s_nb[((tx / B) * R + ty / B) * R + tz / B];
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (rank >= 0) v = gv[(int64_t)rank * NC + (tx % B) + B * ((ty % B) + B * (tz % B))];
-            s_v[t] = v;
-        }
-        __syncthreads();
-        for (int i = s + tid; i < e; i += blockDim.x) {
-            const int64_t p = perm[i];
-            float d[3];
-            int loc[3];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t p = perm[i];
+    const int r = (int)(skey[i] >> S3);
+    Neighbours<B, DENSE> nb;
+    nb.load(P, nbr, r);
+    float d[3];
+    int loc[3];
+    float xp[3];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const float fx = ps[(PX + a) * stride + p] * P.inv_h;
-                const int bi = base_index(fx);
-                d[a] = fx - (float)bi;
-                loc[a] = bi - bc[a] * B;
+    for (int a = 0; a < 3; ++a) {
+        xp[a] = ps[(PX + a) * stride + p];
+        const float fx = xp[a] * P.inv_h;
+        const int bi = base_index(fx);
+        d[a] = fx - (float)bi;
+        loc[a] = bi & (B - 1);
+    }
+    float wx[3], dwx[3], wy[3], dwy[3], wz[3], dwz[3];
+    bspline3(d[0], wx, dwx);
+    bspline3(d[1], wy, dwy);
+    bspline3(d[2], wz, dwz);
+    float vp[3] = {0.f, 0.f, 0.f}, Bx[3] = {0.f, 0.f, 0.f}, By[3] = {0.f, 0.f, 0.f}, Bz[3] = {0.f, 0.f, 0.f};
+    float Lx[3] = {0.f, 0.f, 0.f}, Ly[3] = {0.f, 0.f, 0.f}, Lz[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int lx = loc[0] + a;
+        const int ex = lx / B, mx = lx % B;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const int ly = loc[1] + b;
+            const int ey = ly / B, my = ly % B;
+            int q0, q1, q2;
+            if (B == 4) {
+                q0 = ex ? (ey ? nb.q[6] : nb.q[4]) : (ey ? nb.q[2] : nb.q[0]);
+                q1 = ex ? (ey ? nb.q[7] : nb.q[5]) : (ey ? nb.q[3] : nb.q[1]);
+                q2 = q1;
+            } else {
+                q0 = nb.q[(a * 3 + b) * 3 + 0];
+                q1 = nb.q[(a * 3 + b) * 3 + 1];
+                q2 = nb.q[(a * 3 + b) * 3 + 2];
             }
-            if (loc[0] < 0 || loc[0] >= B || loc[1] < 0 || loc[1] >= B || loc[2] < 0 || loc[2] >= B) {
-                atomicOr(&st->map_miss, 1u);   // cannot happen with a consistent sort
-                continue;
-            }
-            float wx[3], dwx[3], wy[3], dwy[3], wz[3], dwz[3];
-            bspline3(d[0], wx, dwx);
-            bspline3(d[1], wy, dwy);
-            bspline3(d[2], wz, dwz);
-            float vp[3] = {0.f, 0.f, 0.f};
-            float Bm[9], L[9];
+            float Sw[3] = {0.f, 0.f, 0.f}, Sd[3] = {0.f, 0.f, 0.f}, Sc[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-            for (int k = 0; k < 9; ++k) Bm[k] = L[k] = 0.f;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const float ox = (float)a - d[0];
-#pragma unroll
-                for (int b = 0; b < 3; ++b) {
-                    const float oy = (float)b - d[1];
-                    const float wxy = wx[a] * wy[b];
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const float oz = (float)c - d[2];
-                        const float4 vn = s_v[(loc[0] + a) + T * ((loc[1] + b) + T * (loc[2] + c))];
-                        const float N = wxy * wz[c];
-                        const float gx = dwx[a] * wy[b] * wz[c], gy = wx[a] * dwy[b] * wz[c], gz = wxy * dwz[c];
-                        const float nvx = N * vn.x, nvy = N * vn.y, nvz = N * vn.z;
-                        vp[0] += nvx;
-                        vp[1] += nvy;
-                        vp[2] += nvz;
-                        Bm[0] = fmaf(nvx, ox, Bm[0]);
-                        Bm[1] = fmaf(nvx, oy, Bm[1]);
-                        Bm[2] = fmaf(nvx, oz, Bm[2]);
-                        Bm[3] = fmaf(nvy, ox, Bm[3]);
-                        Bm[4] = fmaf(nvy, oy, Bm[4]);
-                        Bm[5] = fmaf(nvy, oz, Bm[5]);
-                        Bm[6] = fmaf(nvz, ox, Bm[6]);
-                        Bm[7] = fmaf(nvz, oy, Bm[7]);
-                        Bm[8] = fmaf(nvz, oz, Bm[8]);
-                        L[0] = fmaf(vn.x, gx, L[0]);
-                        L[1] = fmaf(vn.x, gy, L[1]);
-                        L[2] = fmaf(vn.x, gz, L[2]);
-                        L[3] = fmaf(vn.y, gx, L[3]);
-                        L[4] = fmaf(vn.y, gy, L[4]);
-                        L[5] = fmaf(vn.y, gz, L[5]);
-                        L[6] = fmaf(vn.z, gx, L[6]);
-                        L[7] = fmaf(vn.z, gy, L[7]);
-                        L[8] = fmaf(vn.z, gz, L[8]);
-                    }
+            for (int c = 0; c < 3; ++c) {
+                const int lz = loc[2] + c;
+                const int ez = lz / B, mz = lz % B;
+                const int q = (B == 4) ? (ez ? q1 : q0) : (c == 0 ? q0 : (c == 1 ? q1 : q2));
+                const float4 v = __ldg(&gv[(int64_t)q * NC + mx + B * (my + B * mz)]);
+                Sw[0] = fmaf(wz[c], v.x, Sw[0]);
+                Sw[1] = fmaf(wz[c], v.y, Sw[1]);
+                Sw[2] = fmaf(wz[c], v.z, Sw[2]);
+                Sd[0] = fmaf(dwz[c], v.x, Sd[0]);
+                Sd[1] = fmaf(dwz[c], v.y, Sd[1]);
+                Sd[2] = fmaf(dwz[c], v.z, Sd[2]);
+                if (c > 0) {
+                    const float cw = (float)c * wz[c];
+                    Sc[0] = fmaf(cw, v.x, Sc[0]);
+                    Sc[1] = fmaf(cw, v.y, Sc[1]);
+                    Sc[2] = fmaf(cw, v.z, Sc[2]);
                 }
             }
-            // C = B D^-1 with B = h Bm (offsets in cells) and D = h^2/4 I
-            const float cs = 4.f * P.inv_h;
-            // F <- (I + dt L) F with L = (sum v (x) grad N) (1/h)
-            const float ls = P.dt * P.inv_h;
-            float F[9], Fn[9];
+            const float Pw = wx[a] * wy[b];
+            const float gxw = dwx[a] * wy[b], gyw = wx[a] * dwy[b];
+            const float oa = (float)a - d[0], ob = (float)b - d[1];
 #pragma unroll
-            for (int k = 0; k < 9; ++k) F[k] = ps[(PF + k) * stride + p];
-#pragma unroll
-            for (int i2 = 0; i2 < 3; ++i2)
-#pragma unroll
-                for (int j2 = 0; j2 < 3; ++j2)
-                    Fn[i2 * 3 + j2] = F[i2 * 3 + j2] + ls * (L[i2 * 3 + 0] * F[0 * 3 + j2] + L[i2 * 3 + 1] * F[1 * 3 + j2] +
-                                                            L[i2 * 3 + 2] * F[2 * 3 + j2]);
-            const float alpha = ps[PPHI * stride + p];
-            Sym tau;
-            bool ok;
-            if (MAT == MPM_NEOHOOKEAN) ok = nh_tau(P, Fn, tau);
-            else ok = dp_update(P, alpha, Fn, tau);
-            float xo[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) xo[a] = ps[(PX + a) * stride + p] + P.dt * vp[a];
-            bool fin = ok;
-#pragma unroll
-            for (int k = 0; k < 9; ++k) fin = fin && isfinite(Fn[k]) && isfinite(Bm[k]);
-            fin = fin && isfinite(xo[0]) && isfinite(xo[1]) && isfinite(xo[2]) && isfinite(tau.xx) &&
-                  isfinite(tau.yy) && isfinite(tau.zz) && isfinite(tau.xy) && isfinite(tau.xz) && isfinite(tau.yz);
-            if (!fin) atomicOr(&st->numeric, 1u);
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                po[(PX + a) * stride + i] = xo[a];
-                po[(PV + a) * stride + i] = vp[a];
+            for (int k = 0; k < 3; ++k) {
+                const float Q = Pw * Sw[k];
+                vp[k] += Q;
+                Bx[k] = fmaf(oa, Q, Bx[k]);
+                By[k] = fmaf(ob, Q, By[k]);
+                Bz[k] = fmaf(Pw, fmaf(-d[2], Sw[k], Sc[k]), Bz[k]);
+                Lx[k] = fmaf(gxw, Sw[k], Lx[k]);
+                Ly[k] = fmaf(gyw, Sw[k], Ly[k]);
+                Lz[k] = fmaf(Pw, Sd[k], Lz[k]);
             }
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                po[(PC + k) * stride + i] = cs * Bm[k];
-                po[(PF + k) * stride + i] = Fn[k];
-            }
-            po[(PT + 0) * stride + i] = tau.xx;
-            po[(PT + 1) * stride + i] = tau.xy;
-            po[(PT + 2) * stride + i] = tau.xz;
-            po[(PT + 3) * stride + i] = tau.yy;
-            po[(PT + 4) * stride + i] = tau.yz;
-            po[(PT + 5) * stride + i] = tau.zz;
-            po[PPHI * stride + i] = alpha;
-            po[PID * stride + i] = ps[PID * stride + p];
         }
-        __syncthreads();
     }
+    // C = B D^-1 with B = h [Bx By Bz] and D = h^2/4 I; L = [Lx Ly Lz] / h
+    const float cs = 4.f * P.inv_h;
+    const float ls = P.dt * P.inv_h;
+    float F[9], Fn[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) F[k] = ps[(PF + k) * stride + p];
+    const float L[9] = {Lx[0], Ly[0], Lz[0], Lx[1], Ly[1], Lz[1], Lx[2], Ly[2], Lz[2]};
+#pragma unroll
+    for (int i2 = 0; i2 < 3; ++i2)
+#pragma unroll
+        for (int j2 = 0; j2 < 3; ++j2)
+            Fn[i2 * 3 + j2] = F[i2 * 3 + j2] + ls * (L[i2 * 3 + 0] * F[0 * 3 + j2] + L[i2 * 3 + 1] * F[1 * 3 + j2] +
+                                                    L[i2 * 3 + 2] * F[2 * 3 + j2]);
+    const float alpha = ps[PPHI * stride + p];
+    Sym tau;
+    bool ok;
+    if (MAT == MPM_NEOHOOKEAN) ok = nh_tau(P, Fn, tau);
+    else ok = dp_update(P, alpha, Fn, tau);
+    float xo[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) xo[a] = xp[a] + P.dt * vp[a];
+    const float Cm[9] = {cs * Bx[0], cs * By[0], cs * Bz[0], cs * Bx[1], cs * By[1], cs * Bz[1],
+                         cs * Bx[2], cs * By[2], cs * Bz[2]};
+    bool fin = ok;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) fin = fin && isfinite(Fn[k]) && isfinite(Cm[k]);
+    fin = fin && isfinite(xo[0]) && isfinite(xo[1]) && isfinite(xo[2]) && isfinite(tau.xx) && isfinite(tau.yy) &&
+          isfinite(tau.zz) && isfinite(tau.xy) && isfinite(tau.xz) && isfinite(tau.yz);
+    if (!fin) atomicOr(&st->numeric, 1u);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        po[(PX + a) * stride + i] = xo[a];
+        po[(PV + a) * stride + i] = vp[a];
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        po[(PC + k) * stride + i] = Cm[k];
+        po[(PF + k) * stride + i] = Fn[k];
+    }
+    po[(PT + 0) * stride + i] = tau.xx;
+    po[(PT + 1) * stride + i] = tau.xy;
+    po[(PT + 2) * stride + i] = tau.xz;
+    po[(PT + 3) * stride + i] = tau.yy;
+    po[(PT + 4) * stride + i] = tau.yz;
+    po[(PT + 5) * stride + i] = tau.zz;
+    po[PPHI * stride + i] = alpha;
+    po[PID * stride + i] = ps[PID * stride + p];
 }
 
 // tau (and the cone constant alpha) of an unprojected state.
@@ -704,44 +766,43 @@ __global__ void k_init_stress(float* __restrict__ ps, int64_t stride, int64_t n,
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-constexpr int PERSIST = 148 * 8;   // CTAs for the block loops (grid-stride over a device count)
+constexpr int PERSIST = 148 * 4;   // CTAs of the block P2G (grid-stride over a device count)
 
 }  // namespace
 
 cudaError_t launch_p2g(mpm_ctx* c) {
     const float* ps = c->ps[c->cur];
-    const uint32_t* skey = c->pkey[c->sorted_sel];
     const uint32_t* perm = c->pval[c->sorted_sel];
     HashView hv{c->hkeys, c->hvals, (uint64_t)(c->H ? c->H - 1 : 0)};
-    if (c->det) {
-        const int64_t nn = c->n_active * c->B3;
-#define MPM_GATHER(B_, D_)                                                                                     \
-    k_p2g_gather<B_, D_><<<blocks_for(nn, 128), 128, 0, c->st>>>(ps, c->pstride, perm, c->cellstart, nn, c->P, \
-                                                                  hv, c->bcoord, c->gmv, c->gf)
-        if (c->B == 4) {
-            if (c->dense) MPM_GATHER(4, true);
-            else MPM_GATHER(4, false);
-        } else {
-            if (c->dense) MPM_GATHER(1, true);
-            else MPM_GATHER(1, false);
-        }
-#undef MPM_GATHER
+    if (c->B == 1) {
+        k_p2g_atomic<<<blocks_for(c->n, 256), 256, 0, c->st>>>(ps, c->pstride, perm, c->pkey[c->sorted_sel], c->n,
+                                                              c->nbr, c->P, c->gmv, c->gf, c->dstat);
         ++c->launches;
         return cudaGetLastError();
     }
-#define MPM_TILE(B_, D_)                                                                                             \
-    k_p2g_tile<B_, D_><<<PERSIST, TileCfg<B_>::NT, 0, c->st>>>(ps, c->pstride, skey, perm, c->bstart, c->bend,     \
-                                                                c->pblocks, c->dstat, c->P, hv, c->bcoord, c->gmv, \
-                                                                c->gf, c->dstat)
-    if (c->B == 4) {
-        if (c->dense) MPM_TILE(4, true);
-        else MPM_TILE(4, false);
+#define MPM_CELLS(D_, T_)                                                                                         \
+    k_p2g_cells<D_, T_><<<PERSIST, CellTileCfg::WARPS * 32, 0, c->st>>>(ps, c->pstride, perm, c->bstart, c->bend, \
+                                                                       c->pblocks, c->ccount, c->dstat, c->P,   \
+                                                                       c->nbr, c->gmv, c->gf, c->tbuf, c->dstat)
+    if (c->dense) {
+        if (c->det) MPM_CELLS(true, true);
+        else MPM_CELLS(true, false);
     } else {
-        if (c->dense) MPM_TILE(1, true);
-        else MPM_TILE(1, false);
+        if (c->det) MPM_CELLS(false, true);
+        else MPM_CELLS(false, false);
     }
-#undef MPM_TILE
+#undef MPM_CELLS
     ++c->launches;
+    if (c->det) {
+        const int64_t nn = c->n_active * 64;
+        if (c->dense)
+            k_p2g_reduce<true><<<blocks_for(nn, 256), 256, 0, c->st>>>(nn, c->P, hv, c->bcoord, c->tbuf, c->hasp,
+                                                                      c->gen, c->gmv, c->gf);
+        else
+            k_p2g_reduce<false><<<blocks_for(nn, 256), 256, 0, c->st>>>(nn, c->P, hv, c->bcoord, c->tbuf, c->hasp,
+                                                                       c->gen, c->gmv, c->gf);
+        ++c->launches;
+    }
     return cudaGetLastError();
 }
 
@@ -759,11 +820,10 @@ cudaError_t launch_g2p(mpm_ctx* c) {
     const float* ps = c->ps[c->cur];
     float* po = c->ps[1 - c->cur];
     const uint32_t* perm = c->pval[c->sorted_sel];
-    HashView hv{c->hkeys, c->hvals, (uint64_t)(c->H ? c->H - 1 : 0)};
-    const int nt = (c->B == 4) ? 256 : 32;
-#define MPM_G2P(B_, D_, M_)                                                                                          \
-    k_g2p<B_, D_, M_><<<PERSIST, nt, 0, c->st>>>(ps, po, c->pstride, perm, c->bstart, c->bend, c->pblocks, c->dstat, \
-                                                  c->P, hv, c->bcoord, c->gv, c->dstat)
+    const uint32_t* skey = c->pkey[c->sorted_sel];
+    const unsigned g = blocks_for(c->n, 256);
+#define MPM_G2P(B_, D_, M_)                                                                                       \
+    k_g2p<B_, D_, M_><<<g, 256, 0, c->st>>>(ps, po, c->pstride, perm, skey, c->n, c->nbr, c->P, c->gv, c->dstat)
     const int mat = c->P.material;
     if (c->B == 4) {
         if (c->dense) {

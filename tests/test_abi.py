@@ -75,6 +75,7 @@ def _try_create(native, **over):
     (dict(domain_lo=[-(1 << 20) - 1, 0, 0]), "Eq. (key)"),
     (dict(domain_lo=[0, 0, 0], domain_hi=[1 << 19, 1 << 19, 1 << 10]), "2^32"),
     (dict(_n=0), "particle count"),
+    (dict(flags=1, block_size=1), "block_size 4"),
 ])
 def test_invalid_configs_rejected_on_host(native, over, why):
     st, msg = _try_create(native, **over)
