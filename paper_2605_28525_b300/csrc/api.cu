@@ -213,12 +213,22 @@ cudaError_t ensure_grid(mpm_ctx* c, int64_t nodes) {
     dfree(c, c->gmv, 0);
     dfree(c, c->gf, 0);
     dfree(c, c->gv, 0);
+    dfree(c, c->bins, 0);
+    dfree(c, c->cs, 0);
+    dfree(c, c->tsum, 0);
     c->gmv = c->gf = c->gv = nullptr;
+    c->bins = c->cs = c->tsum = nullptr;
     c->node_cap = 0;
     cudaError_t e;
     if ((e = dalloc(c, (void**)&c->gmv, sizeof(float4) * nc)) != cudaSuccess) return e;
     if ((e = dalloc(c, (void**)&c->gf, sizeof(float4) * nc)) != cudaSuccess) return e;
     if ((e = dalloc(c, (void**)&c->gv, sizeof(float4) * nc)) != cudaSuccess) return e;
+    if (counting_sort(c)) {
+        // one counting-sort bin per (block, cell), i.e. per node
+        if ((e = dalloc(c, (void**)&c->bins, sizeof(int) * nc)) != cudaSuccess) return e;
+        if ((e = dalloc(c, (void**)&c->cs, sizeof(int) * (nc + 1))) != cudaSuccess) return e;
+        if ((e = dalloc(c, (void**)&c->tsum, sizeof(int) * (nc / 2048 + 2))) != cudaSuccess) return e;
+    }
     c->node_cap = nc;
     return cudaSuccess;
 }
@@ -508,6 +518,7 @@ static mpm_status create_impl(const mpm_config* cfg, int64_t n, const float* x, 
         CK(dalloc(c, (void**)&c->pkey[b], sizeof(uint32_t) * n));
         CK(dalloc(c, (void**)&c->pval[b], sizeof(uint32_t) * n));
     }
+    if (counting_sort(c)) CK(dalloc(c, (void**)&c->prank, sizeof(uint32_t) * n));
     if (cfg->terrain_height) {
         const int64_t tn = (int64_t)cfg->terrain_nx * cfg->terrain_ny;
         CK(dalloc(c, (void**)&c->terrain, sizeof(float) * tn));

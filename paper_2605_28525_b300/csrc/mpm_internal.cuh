@@ -194,6 +194,10 @@ struct mpm_ctx {
     int* ccount = nullptr;       // per (Phi, cell): particles in the cell (k-major P2G order)
     int* nbr = nullptr;          // per Phi: Phi of the blocks b + {0..R-1}^3 (R = 2 for B = 4, 3 for B = 1)
     int64_t brange_cap = 0;
+    int* bins = nullptr;         // counting sort: particles per (Phi, cell) bin (one per node)
+    int* cs = nullptr;           // counting sort: exclusive scan of bins (+ total)
+    int* tsum = nullptr;         // counting sort: scan tile totals
+    uint32_t* prank = nullptr;   // counting sort: rank of each particle in its bin
     float* tbuf = nullptr;       // deterministic mode: 7 x 216 tile floats per block
     int64_t tbuf_cap = 0;
     int* hasp = nullptr;         // per Phi: generation of the last step the block held particles
@@ -248,6 +252,7 @@ cudaError_t launch_dense_codes(mpm_ctx* c);
 cudaError_t launch_assign(mpm_ctx* c);
 cudaError_t launch_particle_keys(mpm_ctx* c);
 cudaError_t launch_ranges(mpm_ctx* c, const uint32_t* skey);
+bool counting_sort(const mpm_ctx* c);
 
 // ---- transfers (transfer.cu)
 cudaError_t launch_p2g(mpm_ctx* c);

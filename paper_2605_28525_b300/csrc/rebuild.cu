@@ -24,7 +24,6 @@
 namespace mpm {
 
 namespace {
-constexpr unsigned FULL = 0xffffffffu;
 
 __global__ void k_hash_clear(unsigned long long* __restrict__ keys, int* __restrict__ vals, int64_t H,
                              DevStatus* st) {
@@ -113,32 +112,53 @@ __global__ void __launch_bounds__(256) k_insert(const float* __restrict__ ps, in
     constexpr int NJ = R * R * R;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
+    const unsigned FULL = 0xffffffffu;
     int base[3] = {0, 0, 0};
     bool ok = p < n;
     if (ok) ok = particle_base(ps, stride, p, P, base, st);
-    int b0[3], nbk[3];
+    int b0[3];
+    unsigned need = 0;   // bit j: block b0 + (j / R^2, (j / R) % R, j % R) holds a stencil node
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        b0[a] = base[a] >> S;
-        nbk[a] = ((base[a] + 2) >> S) - b0[a] + 1;
+    for (int a = 0; a < 3; ++a) b0[a] = base[a] >> S;
+    if (ok) {
+        int nbk[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) nbk[a] = ((base[a] + 2) >> S) - b0[a] + 1;
+#pragma unroll
+        for (int j = 0; j < NJ; ++j)
+            if (j / (R * R) < nbk[0] && (j / R) % R < nbk[1] && j % R < nbk[2]) need |= 1u << j;
     }
+    // Lanes with the same base block form one group (particles are sorted, so
+    // a warp usually holds one or two groups).  The group's union of needed
+    // blocks is read from one ballot per block offset, and its members take
+    // the inserts in turn, so the CAS probes of one warp run in parallel.
+    const uint64_t key0 = ok ? pack_key(b0[0], b0[1], b0[2]) : EMPTY_KEY;
+    const unsigned peers = __match_any_sync(FULL, key0);
+    const int leader = __ffs(peers) - 1;
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    const int gsize = __popc(peers);
+    unsigned gneed = 0;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j)
+        if (__ballot_sync(FULL, (need >> j) & 1u) & peers) gneed |= 1u << j;
     int myslot = -1;
-#pragma unroll 1
-    for (int j = 0; j < NJ; ++j) {
-        const int jx = j / (R * R), jy = (j / R) % R, jz = j % R;
-        const bool has = ok && jx < nbk[0] && jy < nbk[1] && jz < nbk[2];
-        const int bi = b0[0] + jx, bj = b0[1] + jy, bk = b0[2] + jz;
-        const uint64_t key = has ? pack_key(bi, bj, bk) : EMPTY_KEY;
-        const unsigned peers = __match_any_sync(FULL, key);
-        const int leader = __ffs(peers) - 1;
-        int slot = -1;
-        if (has && lane == leader) slot = hash_insert(hv, key, rel_key(P, bi, bj, bk), P.max_probe, akey, aslot, cap, st);
-        slot = __shfl_sync(FULL, slot, leader);
-        if (j == 0) myslot = slot;
+    if (ok) {
+        const int nneed = __popc(gneed);
+        for (int t = rank; t < nneed; t += gsize) {
+            // the t-th set bit of gneed
+            unsigned m = gneed;
+            for (int q = 0; q < t; ++q) m &= m - 1u;
+            const int j = __ffs(m) - 1;
+            const int bi = b0[0] + j / (R * R), bj = b0[1] + (j / R) % R, bk = b0[2] + j % R;
+            const int slot = hash_insert(hv, pack_key(bi, bj, bk), rel_key(P, bi, bj, bk), P.max_probe, akey, aslot,
+                                         cap, st);
+            if (j == 0) myslot = slot;   // bit 0 (the base block) is taken by rank 0 = the leader
+        }
     }
+    const int slot0 = __shfl_sync(FULL, myslot, leader);
     if (ok) {
         const int cell = (base[0] & (B - 1)) + B * ((base[1] & (B - 1)) + B * (base[2] & (B - 1)));
-        pcode[p] = myslot < 0 ? 0xffffffffu : (uint32_t)myslot * (uint32_t)(B * B * B) + (uint32_t)cell;
+        pcode[p] = slot0 < 0 ? 0xffffffffu : (uint32_t)slot0 * (uint32_t)(B * B * B) + (uint32_t)cell;
     }
 }
 
@@ -159,7 +179,7 @@ __global__ void __launch_bounds__(256) k_dense_codes(const float* __restrict__ p
 // Phi in key order: the sorted list position is the compact block index.
 __global__ void k_assign(const uint32_t* __restrict__ skey, const uint32_t* __restrict__ sslot, int64_t nact,
                          Params P, int* __restrict__ hvals, int4* __restrict__ bcoord, float4* __restrict__ gmv,
-                         float4* __restrict__ gf, int B3, int zero_grid) {
+                         float4* __restrict__ gf, int* __restrict__ bins, int B3, int zero_grid) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nact * B3) return;
     const int64_t r = i / B3;
@@ -173,6 +193,7 @@ __global__ void k_assign(const uint32_t* __restrict__ skey, const uint32_t* __re
         gmv[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         gf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    if (bins) bins[i] = 0;   // counting-sort bins: one per (block, cell) = one per node
 }
 
 // Phi of the blocks b + {0..R-1}^3 of every active block (runs after
@@ -260,8 +281,8 @@ __device__ __forceinline__ int first_geq(const uint32_t* __restrict__ skey, int 
 __global__ void __launch_bounds__(128) k_interleave(const uint32_t* __restrict__ skey, const uint32_t* __restrict__ perm,
                                                     const int* __restrict__ bstart, const int* __restrict__ bend,
                                                     const int* __restrict__ pblocks, const DevStatus* __restrict__ stc,
-                                                    uint32_t* __restrict__ skey2, uint32_t* __restrict__ perm2,
-                                                    int* __restrict__ ccount) {
+                                                    const int* __restrict__ cs, uint32_t* __restrict__ skey2,
+                                                    uint32_t* __restrict__ perm2, int* __restrict__ ccount) {
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * 4 + (threadIdx.x >> 5), nw = gridDim.x * 4;
     const unsigned FULL = 0xffffffffu, lt = (1u << lane) - 1u;
@@ -270,8 +291,18 @@ __global__ void __launch_bounds__(128) k_interleave(const uint32_t* __restrict__
         const int r = pblocks[kb];
         const int s = bstart[r], e = bend[r];
         const uint32_t base = (uint32_t)r * 64u;
-        const int lo0 = first_geq(skey, s, e, base + lane), hi0 = first_geq(skey, lo0, e, base + lane + 1);
-        const int lo1 = first_geq(skey, s, e, base + 32 + lane), hi1 = first_geq(skey, lo1, e, base + 33 + lane);
+        int lo0, hi0, lo1, hi1;
+        if (cs) {   // cell starts known from the counting sort
+            lo0 = cs[base + lane];
+            hi0 = cs[base + lane + 1];
+            lo1 = cs[base + 32 + lane];
+            hi1 = cs[base + 33 + lane];
+        } else {
+            lo0 = first_geq(skey, s, e, base + lane);
+            hi0 = first_geq(skey, lo0, e, base + lane + 1);
+            lo1 = first_geq(skey, s, e, base + 32 + lane);
+            hi1 = first_geq(skey, lo1, e, base + 33 + lane);
+        }
         const int cnt0 = hi0 - lo0, cnt1 = hi1 - lo1;
         ccount[(int64_t)r * 64 + lane] = cnt0;
         ccount[(int64_t)r * 64 + 32 + lane] = cnt1;
@@ -291,6 +322,133 @@ __global__ void __launch_bounds__(128) k_interleave(const uint32_t* __restrict__
             }
             off += __popc(M0) + __popc(M1);
         }
+    }
+}
+
+// ------------------------------------------------ counting sort (fast mode)
+
+// Sort key per particle and its rank among the particles of its (block, cell)
+// bin: lanes of a warp with the same key take consecutive ranks from one
+// atomic add by their leader.
+__global__ void __launch_bounds__(256) k_particle_bins(int64_t n, const uint32_t* __restrict__ pcode,
+                                                       const int* __restrict__ hvals, int B3, int* __restrict__ bins,
+                                                       uint32_t* __restrict__ key, uint32_t* __restrict__ prank,
+                                                       DevStatus* st) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const unsigned FULL = 0xffffffffu;
+    uint32_t k = 0xffffffffu;
+    if (p < n) {
+        const uint32_t code = pcode[p];
+        const int r = code == 0xffffffffu ? -1 : hvals[code / (uint32_t)B3];
+        if (r < 0) atomicOr(&st->map_miss, 1u);
+        else k = (uint32_t)r * (uint32_t)B3 + code % (uint32_t)B3;
+    }
+    const unsigned peers = __match_any_sync(FULL, k);
+    const int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (k != 0xffffffffu && lane == leader) base = atomicAdd(&bins[k], __popc(peers));
+    base = __shfl_sync(FULL, base, leader);
+    if (p < n) {
+        key[p] = k;
+        prank[p] = (uint32_t)(base + __popc(peers & ((1u << lane) - 1u)));
+    }
+}
+
+constexpr int SC_THREADS = 256, SC_ITEMS = 8, SC_TILE = SC_THREADS * SC_ITEMS;
+
+// Exclusive scan, step 1: each tile of 2048 bins scanned locally; tile totals.
+__global__ void __launch_bounds__(SC_THREADS) k_scan_tiles(const int* __restrict__ in, int64_t n,
+                                                           int* __restrict__ out, int* __restrict__ tsum) {
+    __shared__ int wsum[SC_THREADS / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * SC_TILE + (int64_t)threadIdx.x * SC_ITEMS;
+    int v[SC_ITEMS];
+    int tot = 0;
+#pragma unroll
+    for (int j = 0; j < SC_ITEMS; ++j) {
+        v[j] = base + j < n ? in[base + j] : 0;
+        tot += v[j];
+    }
+    int x = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    int pre = 0;
+    for (int k = 0; k < w; ++k) pre += wsum[k];
+    int run = pre + x - tot;
+#pragma unroll
+    for (int j = 0; j < SC_ITEMS; ++j) {
+        if (base + j < n) out[base + j] = run;
+        run += v[j];
+    }
+    if (threadIdx.x == SC_THREADS - 1) tsum[blockIdx.x] = pre + x;
+}
+
+// Step 2: exclusive scan of the tile totals (one CTA); tsum[ntiles] = total.
+__global__ void __launch_bounds__(1024) k_scan_sums(int* __restrict__ tsum, int ntiles) {
+    __shared__ int wsum[32];
+    __shared__ int carry;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int b = 0; b < ntiles; b += 1024) {
+        const int i = b + threadIdx.x;
+        const int v = i < ntiles ? tsum[i] : 0;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        int pre = 0;
+        for (int k = 0; k < w; ++k) pre += wsum[k];
+        const int excl = carry + pre + x - v;
+        __syncthreads();
+        if (i < ntiles) tsum[i] = excl;
+        if (threadIdx.x == 1023) carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) tsum[ntiles] = carry;
+}
+
+// Step 3: add the tile offsets; cs[n] = total.
+__global__ void k_scan_add(int* __restrict__ cs, int64_t n, const int* __restrict__ tsum, int ntiles) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) cs[i] += tsum[i / SC_TILE];
+    if (i == n) cs[n] = tsum[ntiles];
+}
+
+// Scatter into (block, cell) order.
+__global__ void k_bin_scatter(int64_t n, const uint32_t* __restrict__ key, const uint32_t* __restrict__ prank,
+                              const int* __restrict__ cs, uint32_t* __restrict__ skey, uint32_t* __restrict__ perm) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const uint32_t k = key[p];
+    if (k == 0xffffffffu) return;
+    const int pos = cs[k] + (int)prank[p];
+    skey[pos] = k;
+    perm[pos] = (uint32_t)p;
+}
+
+// Particle range and flag of every active block from the cell starts.
+__global__ void k_block_ranges(int64_t nact, int B3, const int* __restrict__ cs, int* __restrict__ bstart,
+                               int* __restrict__ bend, int* __restrict__ pblocks, int* __restrict__ hasp, int gen,
+                               DevStatus* st) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nact) return;
+    const int s = cs[r * B3], e = cs[r * B3 + B3];
+    if (e > s) {
+        bstart[r] = s;
+        bend[r] = e;
+        hasp[r] = gen;
+        pblocks[atomicAdd(&st->n_pblocks, 1u)] = (int)r;
     }
 }
 
@@ -335,7 +493,8 @@ cudaError_t launch_assign(mpm_ctx* c) {
     const int bits = 64 - __builtin_clzll((unsigned long long)(c->n_dom_blocks > 1 ? c->n_dom_blocks - 1 : 1));
     int sel = radix_sort_pairs(c, c->akey, c->aslot, c->n_active, nullptr, bits, c->st);
     k_assign<<<blocks_for(c->n_active * c->B3, 256), 256, 0, c->st>>>(c->akey[sel], c->aslot[sel], c->n_active, c->P,
-                                                                      c->hvals, c->bcoord, c->gmv, c->gf, c->B3, zero);
+                                                                      c->hvals, c->bcoord, c->gmv, c->gf,
+                                                                      counting_sort(c) ? c->bins : nullptr, c->B3, zero);
     HashView hv{c->hkeys, c->hvals, (uint64_t)(c->H - 1)};
     const int nnb = c->B == 4 ? 8 : 27;
     if (c->B == 4)
@@ -346,8 +505,25 @@ cudaError_t launch_assign(mpm_ctx* c) {
     return cudaGetLastError();
 }
 
+bool counting_sort(const mpm_ctx* c) { return !c->dense && !c->det; }
+
 cudaError_t launch_particle_keys(mpm_ctx* c) {
     const float* ps = c->ps[c->cur];
+    const int64_t nkeys = c->n_active * c->B3;
+    if (counting_sort(c)) {
+        // one pass: key + rank in bin; scan of the bins; scatter
+        k_particle_bins<<<blocks_for(c->n, 256), 256, 0, c->st>>>(c->n, c->pcode, c->hvals, c->B3, c->bins, c->pkey[0],
+                                                                  c->prank, c->dstat);
+        const int ntiles = (int)((nkeys + SC_TILE - 1) / SC_TILE);
+        k_scan_tiles<<<ntiles, SC_THREADS, 0, c->st>>>(c->bins, nkeys, c->cs, c->tsum);
+        k_scan_sums<<<1, 1024, 0, c->st>>>(c->tsum, ntiles);
+        k_scan_add<<<blocks_for(nkeys + 1, 256), 256, 0, c->st>>>(c->cs, nkeys, c->tsum, ntiles);
+        k_bin_scatter<<<blocks_for(c->n, 256), 256, 0, c->st>>>(c->n, c->pkey[0], c->prank, c->cs, c->pkey[1],
+                                                                c->pval[1]);
+        c->launches += 5;
+        c->sorted_sel = 1;
+        return cudaGetLastError();
+    }
     const int by_id = c->det ? 1 : 0;
     if (c->dense)
         k_particle_keys<true><<<blocks_for(c->n, 256), 256, 0, c->st>>>(ps, c->pstride, c->n, c->pcode, nullptr, c->B3,
@@ -358,21 +534,26 @@ cudaError_t launch_particle_keys(mpm_ctx* c) {
     ++c->launches;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int64_t nkeys = c->n_active * c->B3;
     const int bits = 64 - __builtin_clzll((unsigned long long)(nkeys > 1 ? nkeys - 1 : 1));
     c->sorted_sel = radix_sort_pairs(c, c->pkey, c->pval, c->n, nullptr, bits, c->st);
     return cudaGetLastError();
 }
 
 cudaError_t launch_ranges(mpm_ctx* c, const uint32_t* skey) {
-    const int shift = (c->B == 4) ? 6 : 0;
-    k_ranges<<<blocks_for(c->n, 256), 256, 0, c->st>>>(skey, c->n, shift, c->n_active, c->bstart, c->bend, c->pblocks,
-                                                        c->hasp, c->gen, c->dstat);
+    const bool cnt = counting_sort(c);
+    if (cnt) {
+        k_block_ranges<<<blocks_for(c->n_active, 256), 256, 0, c->st>>>(c->n_active, c->B3, c->cs, c->bstart, c->bend,
+                                                                        c->pblocks, c->hasp, c->gen, c->dstat);
+    } else {
+        const int shift = (c->B == 4) ? 6 : 0;
+        k_ranges<<<blocks_for(c->n, 256), 256, 0, c->st>>>(skey, c->n, shift, c->n_active, c->bstart, c->bend,
+                                                            c->pblocks, c->hasp, c->gen, c->dstat);
+    }
     ++c->launches;
     if (c->B == 4) {
         const int o = 1 - c->sorted_sel;
         k_interleave<<<148 * 8, 128, 0, c->st>>>(skey, c->pval[c->sorted_sel], c->bstart, c->bend, c->pblocks, c->dstat,
-                                                c->pkey[o], c->pval[o], c->ccount);
+                                                cnt ? c->cs : nullptr, c->pkey[o], c->pval[o], c->ccount);
         c->sorted_sel = o;
         ++c->launches;
     }
