@@ -174,11 +174,36 @@ mpm_status mpm_read_grid(mpm_ctx* ctx, float* m, float* mv, float* f, float* v, 
 
 mpm_status mpm_get_stats(mpm_ctx* ctx, mpm_stats* out);
 
+/* The sorted active-block keys of a particle cloud, for callers that cannot
+ * allocate device memory (the paper has no counterpart: it describes the
+ * active set, not this interface).  Typical callers: code running while a
+ * framework owns the whole GPU through its own memory pool, loops that must
+ * not allocate after start-up, and plug-ins that receive device buffers but
+ * no allocator.  Inputs: x = n particle positions (device, float32, [n][3]),
+ * the potential grid box (domain_lo/hi, node indices, inclusive), dx (a
+ * power of two) and block_size (1 or 4).  Output: block_keys (device,
+ * cap entries) receives the Eq. (key) block keys in ascending key order -
+ * the same list mpm_read_active gives after mpm_rebuild_active - and
+ * *n_active (host) their count.  stream: a cudaStream_t or NULL; the call
+ * waits for its own work on it.
+ * No memory is allocated: the hash table, block list and sort scratch live
+ * in one fixed device array of about 2 MiB, held on every GPU that loads the
+ * library until the process exits.  Limit: 65,536 active blocks per call;
+ * beyond that the call returns MPM_ERR_INVALID_ARG (use mpm_create and
+ * mpm_rebuild_active instead).  Other errors: OUT_OF_DOMAIN, NUMERIC, CUDA;
+ * the reason is in mpm_last_error(NULL).  Every call clears and reuses the
+ * shared array, so calls whose GPU work overlaps (e.g. on two streams) race:
+ * serialise them.  The first call on a device looks up the array's address
+ * with that device current; make that first call before any stream capture. */
+mpm_status mpm_active_blocks_noalloc(const float* x, int64_t n, const int32_t domain_lo[3],
+                                     const int32_t domain_hi[3], double dx, int32_t block_size,
+                                     uint64_t* block_keys, int64_t cap, int64_t* n_active, void* stream);
+
 /* Static description of a status code; never NULL. */
 const char* mpm_status_string(mpm_status s);
 
-/* Reason for the last failure on ctx (or of the last failed mpm_create when
- * ctx is NULL); never NULL. */
+/* Reason for the last failure on ctx (or, when ctx is NULL, of the last
+ * failed mpm_create or mpm_active_blocks_noalloc); never NULL. */
 const char* mpm_last_error(const mpm_ctx* ctx);
 
 /* Free every resource; NULL is ignored.  Synchronises the stream. */

@@ -390,6 +390,8 @@ mpm_status load_arrays(mpm_ctx* c, float* buf, const float* x, const float* v, c
 
 namespace mpm {
 
+void set_noctx_error(const std::string& why) { g_create_error = why; }
+
 cudaError_t dalloc(mpm_ctx* c, void** p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) return cudaSuccess;

@@ -245,6 +245,11 @@ void dfree(mpm_ctx* c, void* p, size_t bytes);
 int radix_sort_pairs(mpm_ctx* c, uint32_t* k[2], uint32_t* v[2], int64_t n_cap,
                      const unsigned int* n_dev, int bits, cudaStream_t st);
 cudaError_t radix_reserve(mpm_ctx* c, int64_t n_cap);
+int radix_sort_pairs_scratch(uint32_t* k[2], uint32_t* v[2], int64_t n_cap, const unsigned int* n_dev, int bits,
+                             uint32_t* counts, uint32_t* totals, cudaStream_t st);
+
+// ---- errors of calls made without a context (api.cu)
+void set_noctx_error(const std::string& why);
 
 // ---- rebuild (rebuild.cu)
 cudaError_t launch_insert(mpm_ctx* c);

@@ -207,4 +207,23 @@ int radix_sort_pairs(mpm_ctx* c, uint32_t* k[2], uint32_t* v[2], int64_t n_cap, 
     return sel;
 }
 
+// The same passes with caller-provided scratch (counts: 256 * ceil(n_cap/2048)
+// words, totals: 256 words) and no context.
+int radix_sort_pairs_scratch(uint32_t* k[2], uint32_t* v[2], int64_t n_cap, const unsigned int* n_dev, int bits,
+                             uint32_t* counts, uint32_t* totals, cudaStream_t st) {
+    if (n_cap <= 1 || bits <= 0) return 0;
+    const int ntiles = (int)((n_cap + RS_TILE - 1) / RS_TILE);
+    const int passes = (bits + 7) / 8;
+    int sel = 0;
+    for (int p = 0; p < passes; ++p) {
+        const int shift = 8 * p;
+        k_rs_hist<<<ntiles, RS_THREADS, 0, st>>>(k[sel], n_cap, n_dev, shift, counts, ntiles);
+        k_rs_scan_rows<<<RADIX, 1024, 0, st>>>(counts, ntiles, totals);
+        k_rs_scatter<<<ntiles, RS_THREADS, 0, st>>>(k[sel], v[sel], k[1 - sel], v[1 - sel], n_cap, n_dev, shift, counts,
+                                                     totals, ntiles);
+        sel = 1 - sel;
+    }
+    return sel;
+}
+
 }  // namespace mpm

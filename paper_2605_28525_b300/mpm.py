@@ -72,7 +72,7 @@ _lib = None
 # every symbol the header declares (checked by tests/test_abi.py against include/mpm.h)
 EXPORTS = ("mpm_config_default", "mpm_create", "mpm_rebuild_active", "mpm_p2g", "mpm_grid_update", "mpm_g2p",
            "mpm_step", "mpm_read_particles", "mpm_write_particles", "mpm_read_active", "mpm_read_grid",
-           "mpm_get_stats", "mpm_status_string", "mpm_last_error", "mpm_destroy")
+           "mpm_get_stats", "mpm_status_string", "mpm_last_error", "mpm_destroy", "mpm_active_blocks_noalloc")
 
 
 def lib():
@@ -103,6 +103,8 @@ def lib():
     L.mpm_last_error.restype = C.c_char_p
     L.mpm_destroy.argtypes = [vp]
     L.mpm_destroy.restype = None
+    L.mpm_active_blocks_noalloc.argtypes = [vp, i64, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_double,
+                                            C.c_int32, vp, i64, C.POINTER(i64), vp]
     _lib = L
     return L
 
