@@ -98,7 +98,7 @@ def lib():
         L.orc_svd3.argtypes = [dp, dp, dp, dp]
         L.orc_p2g.argtypes = [P, C.c_int64, dp, dp, dp, dp, dp, dp, dp, dp]
         L.orc_p2g_abs.argtypes = [P, C.c_int64, dp, dp, dp, dp, dp, dp, dp, dp]
-        L.orc_p2g_nodes.argtypes = [P, C.c_int64, dp, dp, dp, dp, dp, C.c_int64, ip, dp, dp, dp]
+        L.orc_p2g_nodes.argtypes = [P, C.c_int64, dp, dp, dp, dp, dp, C.c_int64, ip, dp, dp, dp, dp]
         L.orc_grid_update.argtypes = [P, dp, dp, dp, dp]
         L.orc_grid_node.argtypes = [P, ip, C.c_double, dp, dp, dp]
         L.orc_g2p_one.argtypes = [P, dp, C.c_double, dp, dp, dp, dp]
@@ -238,17 +238,19 @@ class Oracle:
             raise ValueError("orc_p2g_abs failed (%d)" % rc)
         return am, amv, af
 
-    def p2g_nodes(self, nodes, x, v=None, C_=None, F=None, phi=None):
+    def p2g_nodes(self, nodes, x, v=None, C_=None, F=None, phi=None, with_scale=False):
         n, x, v, C_, F, phi = self._state(x, v, C_, F, phi)
         q = np.ascontiguousarray(nodes, dtype=np.int32).reshape(-1, 3)
         m = np.zeros(len(q))
         mv = np.zeros((len(q), 3))
         f = np.zeros((len(q), 3))
+        af = np.zeros(len(q))
         rc = lib().orc_p2g_nodes(C.byref(self.p), n, _d(x), _d(v), _d(C_), _d(F),
-                                 _d(phi) if phi is not None else None, len(q), _i(q), _d(m), _d(mv), _d(f))
+                                 _d(phi) if phi is not None else None, len(q), _i(q), _d(m), _d(mv), _d(f),
+                                 _d(af) if with_scale else None)
         if rc:
             raise ValueError("orc_p2g_nodes failed (%d)" % rc)
-        return m, mv, f
+        return (m, mv, f, af) if with_scale else (m, mv, f)
 
     def grid_update(self, m, mv, f):
         m = _f64(m, (-1,))

@@ -485,10 +485,13 @@ int orc_p2g_abs(const orc_params* P, int64_t np, const double* x, const double* 
 
 int orc_p2g_nodes(const orc_params* P, int64_t np, const double* x, const double* v,
                   const double* C, const double* F, const double* phi,
-                  int64_t nq, const int32_t* qn, double* m, double* mv, double* f) {
+                  int64_t nq, const int32_t* qn, double* m, double* mv, double* f, double* af) {
     memset(m, 0, (size_t)nq * sizeof(double));
     memset(mv, 0, (size_t)nq * 3 * sizeof(double));
     memset(f, 0, (size_t)nq * 3 * sizeof(double));
+    if (af) memset(af, 0, (size_t)nq * sizeof(double));
+    double mu, la;
+    lame(P, &mu, &la);
     for (int64_t p = 0; p < np; ++p) {
         int32_t base[3];
         stencil_base(P, &x[3 * p], base);
@@ -505,6 +508,13 @@ int orc_p2g_nodes(const orc_params* P, int64_t np, const double* x, const double
         int rc = p2g_particle(P, &x[3 * p], &v[3 * p], &C[9 * p], &F[9 * p], phi_of(P, phi, p),
                               nodes, dm, dmv, df);
         if (rc) return rc;
+        double tmax = 0.0, w[27], gw[81], tau[9];
+        if (af) {
+            int32_t nn[81];
+            orc_weights(P, &x[3 * p], nn, w, gw);
+            orc_kirchhoff(P, &F[9 * p], phi_of(P, phi, p), tau);
+            for (int a = 0; a < 9; ++a) tmax = fmax(tmax, fabs(tau[a]));
+        }
         for (int q = 0; q < 27; ++q)
             for (int64_t k = 0; k < nq; ++k) {
                 if (nodes[3 * q] != qn[3 * k] || nodes[3 * q + 1] != qn[3 * k + 1] ||
@@ -515,6 +525,9 @@ int orc_p2g_nodes(const orc_params* P, int64_t np, const double* x, const double
                     mv[3 * k + a] += dmv[3 * q + a];
                     f[3 * k + a] += df[3 * q + a];
                 }
+                if (af)
+                    af[k] += (fabs(gw[3 * q]) + fabs(gw[3 * q + 1]) + fabs(gw[3 * q + 2])) * particle_volume(P) *
+                             (tmax + mu + la);
             }
     }
     return 0;

@@ -99,10 +99,11 @@ int orc_p2g_abs(const orc_params* P, int64_t np, const double* x, const double* 
                 const double* C, const double* F, const double* phi,
                 double* am, double* amv, double* af);
 
-/* P2G sums at a list of query nodes only (for spot checks of large runs). */
+/* P2G sums at a list of query nodes only (for spot checks of large runs);
+ * af (may be NULL) receives the force scale of orc_p2g_abs at those nodes. */
 int orc_p2g_nodes(const orc_params* P, int64_t np, const double* x, const double* v,
                   const double* C, const double* F, const double* phi,
-                  int64_t nq, const int32_t* qnodes, double* m, double* mv, double* f);
+                  int64_t nq, const int32_t* qnodes, double* m, double* mv, double* f, double* af);
 
 /* Grid update: v = mv/m + dt (f/m + g) for m > 0 else 0, then boundary
  * conditions.  vn has 3 doubles per node. */
