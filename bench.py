@@ -149,11 +149,25 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+L2_BYTES = 126 * 10 ** 6
+STATE_BYTES_PER_PARTICLE = 2 * 32 * 4      # two SoA buffers of 32 float components
+
+
 def time_steps(sim, nsteps, flush=None):
-    """Per-step device time (ms) of sim.step(1) with CUDA events on the
-    library's stream; the L2 is flushed between steps outside the events."""
+    """Device time (ms) per step with CUDA events on the library's stream.
+    Without `flush`: one sim.step(nsteps) call between the events (the steps
+    are queued on the device, one host synchronisation at the end).  With
+    `flush`: sim.step(1) per step, the L2 flushed between steps outside the
+    events."""
     import torch
     st = torch.cuda.current_stream()
+    if flush is None:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        sim.step(nsteps)
+        b.record(st)
+        b.synchronize()
+        return [a.elapsed_time(b) / nsteps] * nsteps
     out = []
     for _ in range(nsteps):
         if flush is not None:
@@ -279,7 +293,13 @@ def main():
     dist = _init_pg(ws, "nccl")
     dev = torch.device("cuda", local)
     wl = make_workload(args.workload)
-    flush = None if args.no_flush else torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    # Between timed steps the L2 is flushed unless the particle state alone
+    # (read and written once per step) is more than twice its size.
+    big = wl.n * STATE_BYTES_PER_PARTICLE > 2 * L2_BYTES
+    flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    flush = None if (big or args.no_flush) else flush_buf
+    l2_note = ("not flushed: particle state %.0f MB (read + written every step) > 2 x %d MB L2" % (
+        wl.n * STATE_BYTES_PER_PARTICLE / 1e6, L2_BYTES // 10 ** 6)) if flush is None else "flushed between steps"
     stream = torch.cuda.current_stream()
 
     sim = mpm.Simulation.from_workload(wl, stream=stream, device_inputs=True)
@@ -301,7 +321,7 @@ def main():
     value = n_all * args.steps / (total_ms / 1e3)
     st = sim.stats()
 
-    phases = time_phases(sim, max(3, min(args.steps, 10)), flush)
+    phases = time_phases(sim, max(3, min(args.steps, 10)), flush_buf)
     dom = max(("p2g", "g2p"), key=lambda k: phases[k])
     pb, nb = ALG_BYTES[dom]
     alg_bytes = wl.n * pb + st["n_active_nodes"] * nb
@@ -344,7 +364,8 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(wl.describe(), l2="flushed between steps" if flush is not None else "not flushed",
+            "config": dict(wl.describe(), l2=l2_note, step_launch="one mpm_step call of K steps (CUDA graphs)"
+                           if flush is None else "mpm_step(1) per step",
                            parallelism="replicas" if ws > 1 else "single GPU",
                            active_blocks=st["n_active_blocks"], particle_blocks=st["n_particle_blocks"]),
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",

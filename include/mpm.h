@@ -66,6 +66,10 @@ enum { MPM_FLOOR_NONE = 0, MPM_FLOOR_STICKY = 1, MPM_FLOOR_SLIP = 2, MPM_FLOOR_C
                                 and the dense grid; needs block_size 4 */
 #define MPM_DENSE_GRID 2u    /* comparator: identity map over every block of the box; the grid
                                 is cleared and updated over the whole potential domain */
+#define MPM_SYNC_STEPS 4u    /* mpm_step reads the status after every insert (one host
+                                synchronisation per step) instead of queueing the steps */
+#define MPM_NO_GRAPHS 8u     /* mpm_step queues its steps as plain kernel launches instead of
+                                replaying CUDA graphs (same kernels, same results) */
 
 /* Optional device allocator (e.g. a framework's caching allocator).  alloc
  * returns a device pointer of at least `bytes` bytes usable on `stream`, or
@@ -92,7 +96,8 @@ typedef struct mpm_config {
     int32_t terrain_nx, terrain_ny;     /* must equal the box's node counts in x and y */
     double terrain_mu;                  /* Coulomb coefficient on nodes with z_n <= H */
     int32_t wall_layers;                /* sticky node layers at each box face (0: 2) */
-    uint32_t flags;                     /* MPM_DETERMINISTIC | MPM_DENSE_GRID */
+    uint32_t flags;                     /* MPM_DETERMINISTIC | MPM_DENSE_GRID | MPM_SYNC_STEPS |
+                                           MPM_NO_GRAPHS */
     int64_t hash_capacity;              /* initial H, power of two (0: automatic) */
     int64_t block_capacity;             /* initial active-block capacity (0: automatic) */
     int32_t max_probe;                  /* n_probe of Alg. 6 (0: 64) */
@@ -152,7 +157,14 @@ mpm_status mpm_grid_update(mpm_ctx* ctx);
 mpm_status mpm_g2p(mpm_ctx* ctx);
 
 /* nsteps full steps = rebuild + P2G + grid update + G2P each.  On error the
- * particle state is the one after the last completed step. */
+ * particle state is the one after the last completed step, and the stats'
+ * step count says how many completed.  The steps are queued without host
+ * synchronisation (as CUDA graphs, one per step) on capacities sized from
+ * the last active-block count with headroom; the call synchronises once at
+ * the end to read the status.  A step that outgrows the capacities stops the
+ * queue on the device; the call then enlarges them (Alg. 7) and runs the
+ * remaining steps again from the last completed one.  The first step of a
+ * context, and a step after a partial phase sequence, run synchronously. */
 mpm_status mpm_step(mpm_ctx* ctx, int32_t nsteps);
 
 /* Copy the particle state out in id order (any pointer may be NULL). */

@@ -1,12 +1,17 @@
 // C-ABI of the sparse-grid MPM library (include/mpm.h).
 //
-// Host-side orchestration of one step on one stream:
-//   rebuild  = insert (Alg. 6) -> one 32-byte status read (the only host sync
-//              of a step) -> regrowth (Alg. 7) if needed -> canonical
+// Host-side orchestration on one stream.  One step:
+//   rebuild  = insert (Alg. 6) -> regrowth (Alg. 7) if needed -> canonical
 //              compaction -> particle sort -> block ranges
-//   p2g      = tile scatter (or fixed-order gather)
+//   p2g      = cell-lane tile scatter (or fixed-order tile reduction)
 //   grid     = explicit Euler + boundary conditions
 //   g2p      = gather + constitutive update into the other particle buffer
+// The phase calls (and a context's first step) read the status after the
+// insert, so the host knows the block count before the compaction.  mpm_step
+// instead queues whole steps with no host synchronisation: every kernel
+// takes its launch size from capacities and its live counts from the status
+// words, a raised error flag makes the rest of the queue return at entry,
+// and one status read at the end tells how many steps completed.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -261,6 +266,23 @@ cudaError_t ensure_block_arrays(mpm_ctx* c, int64_t nb) {
     return cudaSuccess;
 }
 
+// Active blocks that every per-step array can hold.
+void update_live_cap(mpm_ctx* c) {
+    int64_t live = c->dense ? c->n_dom_blocks : c->block_cap;
+    live = std::min(live, c->brange_cap);
+    live = std::min(live, c->node_cap / c->B3);
+    if (c->det) live = std::min<int64_t>(live, c->tbuf_cap / (7 * 216));
+    c->live_cap = live;
+}
+
+// Clear the flags a step may raise and retry from (overflow, out of domain)
+// and the abort word.  numeric and map_miss stay until they are reported.
+cudaError_t clear_retry_flags(mpm_ctx* c) {
+    cudaError_t e = cudaMemsetAsync(&c->dstat->overflow, 0, 2 * sizeof(unsigned int), c->st);
+    if (e != cudaSuccess) return e;
+    return cudaMemsetAsync(&c->dstat->abort, 0, 2 * sizeof(unsigned int), c->st);   // abort, steps_done
+}
+
 // Numeric failure of the last G2P: fall back to the buffer it read.
 void rollback_g2p(mpm_ctx* c) {
     if (c->g2p_swapped) {
@@ -275,9 +297,11 @@ mpm_status do_rebuild(mpm_ctx* c) {
     // keep the table at most half full (Alg. 7 would recover too, at the cost
     // of a second insert)
     if (!c->dense && 2 * c->n_active > c->H) CK(alloc_hash(c, 2 * c->H, std::max<int64_t>(c->block_cap, 2 * c->n_active)));
+    c->ls = c->st;
     for (int round = 0;; ++round) {
+        CK(clear_retry_flags(c));
         if (c->dense) CK(launch_dense_codes(c));
-        else CK(launch_insert(c));
+        else CK(launch_insert(c, c->block_cap));
         CK(read_status(c));
         const DevStatus& s = *c->hstat;
         if (s.map_miss) {
@@ -307,7 +331,7 @@ mpm_status do_rebuild(mpm_ctx* c) {
     CK(ensure_grid(c, nodes));
     CK(ensure_block_arrays(c, c->n_active));
     if (c->det) CK(grow(c, c->tbuf, c->tbuf_cap, c->n_active * 7 * 216, 1.25));
-    ++c->gen;
+    update_live_cap(c);
     CK(launch_assign(c));
     CK(launch_particle_keys(c));
     CK(launch_ranges(c, c->pkey[c->sorted_sel]));
@@ -348,6 +372,151 @@ mpm_status settle(mpm_ctx* c) {
     if (c->hstat->numeric) {
         rollback_g2p(c);
         return fail(c, MPM_ERR_NUMERIC, "non-finite or inverted particle state");
+    }
+    c->g2p_swapped = false;
+    return MPM_OK;
+}
+
+mpm_status sync_step(mpm_ctx* c) {
+    mpm_status s = do_rebuild(c);
+    if (s == MPM_OK) s = do_p2g(c);
+    if (s == MPM_OK) s = do_grid(c);
+    if (s == MPM_OK) s = do_g2p(c);
+    return s;
+}
+
+// The kernels of one step on c->ls, reading particle buffer c->cur.
+mpm_status queue_step(mpm_ctx* c) {
+    if (c->dense) CK(launch_dense_codes(c));
+    else CK(launch_insert(c, c->live_cap));
+    CK(launch_assign(c));
+    CK(launch_particle_keys(c));
+    CK(launch_ranges(c, c->pkey[c->sorted_sel]));
+    CK(launch_p2g(c));
+    CK(launch_grid_update(c));
+    CK(launch_g2p(c));
+    CK(launch_step_done(c));
+    return MPM_OK;
+}
+
+// Capture one step reading buffer `parity` into an executable graph.
+mpm_status capture_step(mpm_ctx* c, int parity) {
+    if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    if (c->graph[parity]) {
+        CK(cudaGraphExecDestroy(c->graph[parity]));
+        c->graph[parity] = nullptr;
+    }
+    const int saved_cur = c->cur;
+    const int64_t l0 = c->launches;
+    c->cur = parity;
+    c->ls = c->cap_stream;
+    cudaGraph_t g = nullptr;
+    mpm_status s = MPM_OK;
+    cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        s = queue_step(c);
+        const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
+        if (s == MPM_OK && e2 != cudaSuccess) e = e2;
+    }
+    c->ls = c->st;
+    c->cur = saved_cur;
+    const int64_t nl = c->launches - l0;
+    c->launches = l0;
+    if (s != MPM_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return s != MPM_OK ? s : cuda_fail(c, e, "step capture");
+    }
+    e = cudaGraphInstantiate(&c->graph[parity], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->graph[parity] = nullptr;
+        return cuda_fail(c, e, "cudaGraphInstantiate");
+    }
+    c->graph_launches[parity] = nl;
+    c->graph_version[parity] = c->cap_version;
+    return MPM_OK;
+}
+
+// Capacities of a batch: the last block count plus half of it as headroom.
+mpm_status prepare_batch(mpm_ctx* c) {
+    const int64_t est = std::max(c->est_active, c->n_active);
+    const int64_t want = c->dense ? c->n_dom_blocks : est + est / 2 + 64;
+    if (!c->dense) {
+        const int64_t H = std::max<int64_t>({next_pow2(2 * want), c->H, c->min_H});
+        if (c->block_cap < want || c->H < H) CK(alloc_hash(c, H, std::max(c->block_cap, want)));
+    }
+    CK(ensure_grid(c, want * c->B3));
+    CK(ensure_block_arrays(c, want));
+    if (c->det) CK(grow(c, c->tbuf, c->tbuf_cap, want * 7 * 216, 1.25));
+    update_live_cap(c);
+    if (!(c->cfg.flags & MPM_NO_GRAPHS)) {
+        for (int p = 0; p < 2; ++p)
+            if (!c->graph[p] || c->graph_version[p] != c->cap_version) {
+                mpm_status s = capture_step(c, p);
+                if (s != MPM_OK) return s;
+            }
+    }
+    return MPM_OK;
+}
+
+// `left` steps queued without host synchronisation; on return `left` holds
+// the steps still to run (0 on success).
+mpm_status run_batch(mpm_ctx* c, int32_t& left) {
+    int failures = 0;
+    while (left > 0) {
+        mpm_status s = prepare_batch(c);
+        if (s != MPM_OK) return s;
+        CK(clear_retry_flags(c));
+        const int c0 = c->cur;
+        const bool graphs = !(c->cfg.flags & MPM_NO_GRAPHS);
+        for (int32_t k = 0; k < left; ++k) {
+            const int p = (c0 + k) & 1;
+            if (graphs) {
+                CK(cudaGraphLaunch(c->graph[p], c->st));
+                c->launches += c->graph_launches[p];
+            } else {
+                c->cur = p;
+                s = queue_step(c);
+                if (s != MPM_OK) {
+                    c->cur = c0;
+                    return s;
+                }
+            }
+        }
+        c->cur = c0;
+        CK(read_status(c));
+        const DevStatus st = *c->hstat;
+        const int32_t done = (int32_t)std::min<unsigned>(st.steps_done, (unsigned)left);
+        c->cur = (c0 + done) & 1;
+        c->steps += done;
+        left -= done;
+        c->phase = 0;
+        c->g2p_swapped = false;
+        if (done > 0) failures = 0;
+        if (!st.abort) {
+            c->n_active = std::min<int64_t>(st.n_active, c->live_cap);
+            c->est_active = c->n_active;
+            continue;
+        }
+        // the failing step's compaction may be partial: no active set is valid now
+        c->n_active = c->dense ? c->n_dom_blocks : 0;
+        if (st.map_miss) {
+            cudaMemsetAsync(&c->dstat->map_miss, 0, sizeof(unsigned int), c->st);
+            return fail(c, MPM_ERR_CUDA, "internal error: inconsistent active map or particle order (code " +
+                                             std::to_string(st.map_miss) + ")");
+        }
+        if (st.numeric) {
+            cudaMemsetAsync(&c->dstat->numeric, 0, sizeof(unsigned int), c->st);
+            return fail(c, MPM_ERR_NUMERIC, "non-finite or inverted particle state");
+        }
+        if (st.out_of_domain) return fail(c, MPM_ERR_OUT_OF_DOMAIN, "a particle stencil left the potential grid box");
+        if (!st.overflow) return fail(c, MPM_ERR_CUDA, "internal error: a step stopped without a reason");
+        // Alg. 7: enlarge and run the remaining steps again
+        if (++failures > c->cfg.max_rebuilds)
+            return fail(c, MPM_ERR_HASH_OVERFLOW, "hash table still overflows after max_rebuilds regrowth rounds");
+        ++c->rebuild_rounds;
+        if (st.overflow & 1u) c->min_H = 2 * c->H;
+        c->est_active = std::max<int64_t>(st.overflow & 2u ? 2 * c->live_cap : c->live_cap, (int64_t)st.n_active);
     }
     return MPM_OK;
 }
@@ -408,6 +577,7 @@ cudaError_t dalloc(mpm_ctx* c, void** p, size_t bytes) {
     }
     registries()[c].sizes[*p] = bytes;
     c->device_bytes += (int64_t)bytes;
+    ++c->cap_version;   // captured steps hold buffer addresses
     return cudaSuccess;
 }
 
@@ -420,6 +590,7 @@ void dfree(mpm_ctx* c, void* p, size_t) {
     if (c->cfg.free) c->cfg.free(p, bytes, (void*)c->st, c->cfg.alloc_user);
     else cudaFree(p);
     c->device_bytes -= (int64_t)bytes;
+    ++c->cap_version;
 }
 
 }  // namespace mpm
@@ -472,6 +643,7 @@ static mpm_status create_impl(const mpm_config* cfg, int64_t n, const float* x, 
     if (!c->cfg.max_rebuilds) c->cfg.max_rebuilds = 12;
     if (!c->cfg.wall_layers) c->cfg.wall_layers = 2;
     c->st = (cudaStream_t)stream;
+    c->ls = c->st;
     CK(cudaGetDevice(&c->device));
     c->dense = (cfg->flags & MPM_DENSE_GRID) != 0;
     c->det = (cfg->flags & MPM_DETERMINISTIC) != 0;
@@ -601,14 +773,24 @@ mpm_status mpm_g2p(mpm_ctx* c) {
 
 mpm_status mpm_step(mpm_ctx* c, int32_t nsteps) {
     if (!c || nsteps < 0) return MPM_ERR_INVALID_ARG;
-    for (int32_t k = 0; k < nsteps; ++k) {
-        mpm_status s = do_rebuild(c);
-        if (s == MPM_OK) s = do_p2g(c);
-        if (s == MPM_OK) s = do_grid(c);
-        if (s == MPM_OK) s = do_g2p(c);
-        if (s != MPM_OK) return s;
+    int32_t left = nsteps;
+    if (c->cfg.flags & MPM_SYNC_STEPS) {
+        for (; left > 0; --left) {
+            mpm_status s = sync_step(c);
+            if (s != MPM_OK) return s;
+        }
+        return settle(c);
     }
-    return settle(c);
+    // a step cut short through the phase calls, or no block count yet: one
+    // synchronous step (it also reports what an earlier G2P left pending)
+    if (left > 0 && (c->phase != 0 || c->g2p_swapped || (!c->dense && c->n_active == 0))) {
+        mpm_status s = sync_step(c);
+        if (s == MPM_OK) s = settle(c);
+        if (s != MPM_OK) return s;
+        --left;
+    }
+    if (left == 0) return nsteps == 0 ? settle(c) : MPM_OK;
+    return run_batch(c, left);
 }
 
 mpm_status mpm_read_particles(mpm_ctx* c, float* x, float* v, float* Cm, float* F, int on_device) {
@@ -743,6 +925,9 @@ mpm_status mpm_get_stats(mpm_ctx* c, mpm_stats* o) {
 void mpm_destroy(mpm_ctx* c) {
     if (!c) return;
     (void)sync_wait(c);
+    for (int p = 0; p < 2; ++p)
+        if (c->graph[p]) cudaGraphExecDestroy(c->graph[p]);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     auto it = registries().find(c);
     if (it != registries().end()) {
         for (auto& kv : it->second.sizes) {

@@ -34,15 +34,43 @@ constexpr uint64_t EMPTY_KEY = ~0ull;
 constexpr int KEY_BITS = 21;               // m of Eq. (key)
 constexpr int KEY_BIAS = 1 << 20;          // b of Eq. (key)
 
+// Device status words.  Every error flag is sticky: the host clears it once
+// it has reported it.  Setting one also sets `abort`, after which each later
+// kernel of the step (and of every queued step) returns at entry, so a batch
+// of steps queued without host synchronisation stops at the first failure.
 struct DevStatus {
-    unsigned int n_active;       // Alg. 6 counter
+    unsigned int n_active;       // Alg. 6 counter (the box's block count on the dense grid)
     unsigned int overflow;       // bit 0: probe limit / table full, bit 1: block capacity
     unsigned int out_of_domain;
     unsigned int numeric;        // non-finite state
     unsigned int n_pblocks;      // blocks holding particles
     unsigned int map_miss;       // a stencil block missing from the map (must stay 0)
-    unsigned int pad[2];
+    unsigned int abort;          // any error flag above was raised
+    unsigned int steps_done;     // steps completed without error since the host cleared it
+    unsigned int gen;            // step generation (block "holds particles" marks)
+    unsigned int go;             // the running step's insert may proceed (written by the table clear)
+    unsigned int pad[6];
 };
+
+__device__ __forceinline__ void raise_flag(DevStatus* s, unsigned int* word, unsigned int bits) {
+    atomicOr(word, bits);
+    atomicOr(&s->abort, 1u);
+}
+
+// CTA-uniform test of the abort word at kernel entry.  Every thread of the
+// CTA must call it (it holds a barrier).
+__device__ __forceinline__ bool cta_aborted(const DevStatus* s) {
+    __shared__ unsigned int ab;
+    if (threadIdx.x == 0) ab = *((volatile const unsigned int*)&s->abort);
+    __syncthreads();
+    return ab != 0u;
+}
+
+// Live active-block count, clamped to the capacity the arrays were sized for.
+__device__ __forceinline__ int64_t live_blocks(const DevStatus* s, int64_t cap) {
+    const int64_t n = (int64_t)*((volatile const unsigned int*)&s->n_active);
+    return n < cap ? n : cap;
+}
 
 // Scalar parameters handed to kernels by value.
 struct Params {
@@ -179,6 +207,7 @@ struct mpm_ctx {
     uint32_t* aslot[2] = {nullptr, nullptr};
     int4* bcoord = nullptr;      // per Phi: block coordinates
     int64_t block_cap = 0;
+    int64_t live_cap = 0;        // active blocks every per-step array can hold (<= block_cap)
     int64_t n_dom_blocks = 0;
     int64_t n_active = 0;        // blocks after the last rebuild
     int64_t n_pblocks = 0;
@@ -200,8 +229,7 @@ struct mpm_ctx {
     uint32_t* prank = nullptr;   // counting sort: rank of each particle in its bin
     float* tbuf = nullptr;       // deterministic mode: 7 x 216 tile floats per block
     int64_t tbuf_cap = 0;
-    int* hasp = nullptr;         // per Phi: generation of the last step the block held particles
-    int gen = 0;                 // rebuild generation
+    int* hasp = nullptr;         // per Phi: generation (DevStatus.gen) of the last step the block held particles
 
     // grid
     float4* gmv = nullptr;
@@ -224,6 +252,14 @@ struct mpm_ctx {
 
     int64_t rebuild_rounds = 0;
     int64_t launches = 0;              // kernels launched by this context
+    cudaStream_t ls = nullptr;         // stream kernels are enqueued on (st, or the capture stream)
+    cudaStream_t cap_stream = nullptr; // private stream for graph capture
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};   // one step, per parity of the read buffer
+    int64_t graph_launches[2] = {0, 0};              // kernels in each captured step
+    int64_t cap_version = 0;           // bumped whenever a buffer is reallocated
+    int64_t graph_version[2] = {-1, -1};
+    int64_t est_active = 0;            // active-block estimate the next batch is sized from
+    int64_t min_H = 0;                 // table size a batch must have (raised by a probe overflow)
     int64_t steps = 0;
     int64_t device_bytes = 0;
     int phase = 0;                     // 0 idle, 1 rebuilt, 2 p2g done, 3 grid done
@@ -243,7 +279,7 @@ void dfree(mpm_ctx* c, void* p, size_t bytes);
 // count.  Buffers k[0]/v[0] hold the input; returns the index of the buffer
 // pair that holds the result.
 int radix_sort_pairs(mpm_ctx* c, uint32_t* k[2], uint32_t* v[2], int64_t n_cap,
-                     const unsigned int* n_dev, int bits, cudaStream_t st);
+                     const unsigned int* n_dev, int bits, cudaStream_t st, const unsigned int* abort = nullptr);
 cudaError_t radix_reserve(mpm_ctx* c, int64_t n_cap);
 int radix_sort_pairs_scratch(uint32_t* k[2], uint32_t* v[2], int64_t n_cap, const unsigned int* n_dev, int bits,
                              uint32_t* counts, uint32_t* totals, cudaStream_t st);
@@ -252,7 +288,7 @@ int radix_sort_pairs_scratch(uint32_t* k[2], uint32_t* v[2], int64_t n_cap, cons
 void set_noctx_error(const std::string& why);
 
 // ---- rebuild (rebuild.cu)
-cudaError_t launch_insert(mpm_ctx* c);
+cudaError_t launch_insert(mpm_ctx* c, int64_t ins_cap);
 cudaError_t launch_dense_codes(mpm_ctx* c);
 cudaError_t launch_assign(mpm_ctx* c);
 cudaError_t launch_particle_keys(mpm_ctx* c);
@@ -264,5 +300,6 @@ cudaError_t launch_p2g(mpm_ctx* c);
 cudaError_t launch_grid_update(mpm_ctx* c);
 cudaError_t launch_g2p(mpm_ctx* c);
 cudaError_t launch_init_stress(mpm_ctx* c, float* buf);
+cudaError_t launch_step_done(mpm_ctx* c);
 
 }  // namespace mpm

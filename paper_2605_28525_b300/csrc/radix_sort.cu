@@ -19,7 +19,9 @@ constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
 constexpr int RADIX = 256;
 constexpr unsigned FULL = 0xffffffffu;
 
-__device__ __forceinline__ int64_t live_count(const unsigned int* n_dev, int64_t n_cap) {
+__device__ __forceinline__ int64_t live_count(const unsigned int* n_dev, int64_t n_cap,
+                                              const unsigned int* abort) {
+    if (abort && *((volatile const unsigned int*)abort)) return 0;   // the step was abandoned
     if (!n_dev) return n_cap;
     int64_t n = (int64_t)(*n_dev);
     return n < n_cap ? n : n_cap;
@@ -33,12 +35,13 @@ __device__ __forceinline__ int64_t item_index(int t, int w, int j, int lane) {
 
 __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint32_t* __restrict__ keys, int64_t n_cap,
                                                          const unsigned int* n_dev, int shift,
-                                                         uint32_t* __restrict__ counts, int ntiles) {
+                                                         uint32_t* __restrict__ counts, int ntiles,
+                                                         const unsigned int* abort) {
     __shared__ uint32_t hist[RS_WARPS][RADIX];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int i = threadIdx.x; i < RS_WARPS * RADIX; i += RS_THREADS) (&hist[0][0])[i] = 0;
     __syncthreads();
-    const int64_t n = live_count(n_dev, n_cap);
+    const int64_t n = live_count(n_dev, n_cap, abort);
 #pragma unroll
     for (int j = 0; j < RS_ITEMS; ++j) {
         int64_t idx = item_index(blockIdx.x, w, j, lane);
@@ -101,12 +104,13 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t* __res
                                                             uint32_t* __restrict__ vout, int64_t n_cap,
                                                             const unsigned int* n_dev, int shift,
                                                             const uint32_t* __restrict__ counts,
-                                                            const uint32_t* __restrict__ totals, int ntiles) {
+                                                            const uint32_t* __restrict__ totals, int ntiles,
+                                                            const unsigned int* abort) {
     __shared__ uint32_t off[RS_WARPS][RADIX];
     __shared__ uint32_t dbase[RADIX];
     __shared__ uint32_t wsum[RS_WARPS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t n = live_count(n_dev, n_cap);
+    const int64_t n = live_count(n_dev, n_cap, abort);
 
     // global start of every digit for this tile: exclusive scan of the digit
     // totals plus this tile's scanned count
@@ -190,17 +194,17 @@ cudaError_t radix_reserve(mpm_ctx* c, int64_t n_cap) {
 }
 
 int radix_sort_pairs(mpm_ctx* c, uint32_t* k[2], uint32_t* v[2], int64_t n_cap, const unsigned int* n_dev,
-                     int bits, cudaStream_t st) {
+                     int bits, cudaStream_t st, const unsigned int* abort) {
     if (n_cap <= 1 || bits <= 0) return 0;
     const int ntiles = (int)((n_cap + RS_TILE - 1) / RS_TILE);
     const int passes = (bits + 7) / 8;
     int sel = 0;
     for (int p = 0; p < passes; ++p) {
         const int shift = 8 * p;
-        k_rs_hist<<<ntiles, RS_THREADS, 0, st>>>(k[sel], n_cap, n_dev, shift, c->rs.counts, ntiles);
+        k_rs_hist<<<ntiles, RS_THREADS, 0, st>>>(k[sel], n_cap, n_dev, shift, c->rs.counts, ntiles, abort);
         k_rs_scan_rows<<<RADIX, 1024, 0, st>>>(c->rs.counts, ntiles, c->rs.totals);
         k_rs_scatter<<<ntiles, RS_THREADS, 0, st>>>(k[sel], v[sel], k[1 - sel], v[1 - sel], n_cap, n_dev, shift,
-                                                     c->rs.counts, c->rs.totals, ntiles);
+                                                     c->rs.counts, c->rs.totals, ntiles, abort);
         sel = 1 - sel;
         c->launches += 3;
     }
@@ -217,10 +221,10 @@ int radix_sort_pairs_scratch(uint32_t* k[2], uint32_t* v[2], int64_t n_cap, cons
     int sel = 0;
     for (int p = 0; p < passes; ++p) {
         const int shift = 8 * p;
-        k_rs_hist<<<ntiles, RS_THREADS, 0, st>>>(k[sel], n_cap, n_dev, shift, counts, ntiles);
+        k_rs_hist<<<ntiles, RS_THREADS, 0, st>>>(k[sel], n_cap, n_dev, shift, counts, ntiles, nullptr);
         k_rs_scan_rows<<<RADIX, 1024, 0, st>>>(counts, ntiles, totals);
         k_rs_scatter<<<ntiles, RS_THREADS, 0, st>>>(k[sel], v[sel], k[1 - sel], v[1 - sel], n_cap, n_dev, shift, counts,
-                                                     totals, ntiles);
+                                                     totals, ntiles, nullptr);
         sel = 1 - sel;
     }
     return sel;

@@ -1,7 +1,8 @@
 // Active-set rebuild: Sec. 4.3, Alg. 5-7, with a canonical compaction.
 //
-//   k_hash_clear      Alg. 5: keys <- EMPTY, values <- invalid, counter <- 0,
-//                     overflow flag <- false.
+//   k_hash_clear      Alg. 5: keys <- EMPTY, values <- invalid, counter <- 0
+//                     (the overflow flag is already clear: the host clears it
+//                     before a retry, and a raised flag stops the step).
 //   k_insert          Alg. 6: per particle, the blocks of its 27 stencil nodes
 //                     (at most 8 for B = 4, 27 for B = 1), deduplicated inside
 //                     the warp with match.any so one lane per distinct key
@@ -19,32 +20,43 @@
 //   k_interleave      k-major particle order inside every block (the k-th
 //                     particle of each cell, then the next), and the particle
 //                     count per cell, for the cell-lane P2G.
+#include <algorithm>
+
 #include "mpm_internal.cuh"
 
 namespace mpm {
 
 namespace {
 
+// Start of a step.  Nothing here sets the abort word, so every thread reads
+// the same value.  `go` tells the insert whether to run: the insert cannot
+// test `abort` itself, since its own overflow would stop its later CTAs and
+// the block count the host regrows from would come out short.
 __global__ void k_hash_clear(unsigned long long* __restrict__ keys, int* __restrict__ vals, int64_t H,
                              DevStatus* st) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < H) {
-        keys[i] = EMPTY_KEY;
-        vals[i] = -1;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool ab = *((volatile unsigned int*)&st->abort) != 0u;
+    if (i == 0) st->go = ab ? 0u : 1u;
+    if (ab) return;
+    for (int64_t j = i; j < H; j += (int64_t)gridDim.x * blockDim.x) {
+        keys[j] = EMPTY_KEY;
+        vals[j] = -1;
     }
     if (i == 0) {
         st->n_active = 0;
-        st->overflow = 0;
-        st->out_of_domain = 0;
         st->n_pblocks = 0;
+        st->gen += 1u;
     }
 }
 
-__global__ void k_status_clear(DevStatus* st) {
-    st->n_active = 0;
-    st->overflow = 0;
-    st->out_of_domain = 0;
+// Dense grid: the identity map has every block of the box.
+__global__ void k_status_clear(DevStatus* st, unsigned int n_dom_blocks) {
+    const bool ab = st->abort != 0u;
+    st->go = ab ? 0u : 1u;
+    if (ab) return;
+    st->n_active = n_dom_blocks;
     st->n_pblocks = 0;
+    st->gen += 1u;
 }
 
 // Alg. 6 for one key; returns the slot holding it or -1 when n_probe slots
@@ -64,7 +76,7 @@ __device__ int hash_insert(const HashView& hv, uint64_t key, uint32_t rkey, int 
                     akey[idx] = rkey;
                     aslot[idx] = (uint32_t)s;
                 } else {
-                    atomicOr(&st->overflow, 2u);
+                    raise_flag(st, &st->overflow, 2u);
                 }
                 return (int)s;
             }
@@ -72,7 +84,7 @@ __device__ int hash_insert(const HashView& hv, uint64_t key, uint32_t rkey, int 
         }
         s = (s + 1) & hv.mask;
     }
-    atomicOr(&st->overflow, 1u);
+    raise_flag(st, &st->overflow, 1u);
     return -1;
 }
 
@@ -85,14 +97,14 @@ __device__ __forceinline__ bool particle_base(const float* __restrict__ ps, int6
     for (int a = 0; a < 3; ++a) {
         float fx = ps[(PX + a) * stride + p] * P.inv_h;
         if (!isfinite(fx)) {
-            atomicOr(&st->numeric, 1u);
+            raise_flag(st, &st->numeric, 1u);
             ok = false;
             base[a] = 0;
             continue;
         }
         // the stencil base..base+2 must lie inside the node box
         if (!(fx >= (float)P.lo[a] + 0.5f && fx < (float)(P.hi[a] - 2) + 1.5f)) {
-            atomicOr(&st->out_of_domain, 1u);
+            raise_flag(st, &st->out_of_domain, 1u);
             ok = false;
             base[a] = 0;
             continue;
@@ -110,6 +122,7 @@ __global__ void __launch_bounds__(256) k_insert(const float* __restrict__ ps, in
     constexpr int S = (B == 4) ? 2 : 0;
     constexpr int R = (B == 4) ? 2 : 3;   // blocks a stencil can span per axis
     constexpr int NJ = R * R * R;
+    if (*((volatile unsigned int*)&st->go) == 0u) return;   // written by the clear before this kernel: uniform
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
@@ -168,6 +181,7 @@ template <int B>
 __global__ void __launch_bounds__(256) k_dense_codes(const float* __restrict__ ps, int64_t stride, int64_t n,
                                                      Params P, uint32_t* __restrict__ pcode, DevStatus* st) {
     constexpr int S = (B == 4) ? 2 : 0;
+    if (st->go == 0u) return;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     int base[3];
@@ -177,9 +191,12 @@ __global__ void __launch_bounds__(256) k_dense_codes(const float* __restrict__ p
 }
 
 // Phi in key order: the sorted list position is the compact block index.
-__global__ void k_assign(const uint32_t* __restrict__ skey, const uint32_t* __restrict__ sslot, int64_t nact,
-                         Params P, int* __restrict__ hvals, int4* __restrict__ bcoord, float4* __restrict__ gmv,
-                         float4* __restrict__ gf, int* __restrict__ bins, int B3, int zero_grid) {
+__global__ void k_assign(const uint32_t* __restrict__ skey, const uint32_t* __restrict__ sslot, int64_t cap,
+                         const DevStatus* st, Params P, int* __restrict__ hvals, int4* __restrict__ bcoord,
+                         float4* __restrict__ gmv, float4* __restrict__ gf, int* __restrict__ bins, int B3,
+                         int zero_grid) {
+    if (cta_aborted(st)) return;
+    const int64_t nact = live_blocks(st, cap);
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nact * B3) return;
     const int64_t r = i / B3;
@@ -199,10 +216,12 @@ __global__ void k_assign(const uint32_t* __restrict__ skey, const uint32_t* __re
 // Phi of the blocks b + {0..R-1}^3 of every active block (runs after
 // k_assign, once every table value holds its rank).
 template <int B>
-__global__ void k_neighbours(const int4* __restrict__ bcoord, int64_t nact, Params P, HashView hv,
-                             int* __restrict__ nbr) {
+__global__ void k_neighbours(const int4* __restrict__ bcoord, int64_t cap, const DevStatus* st, Params P,
+                             HashView hv, int* __restrict__ nbr) {
     constexpr int R = (B == 4) ? 2 : 3;
     constexpr int NNB = R * R * R;
+    if (cta_aborted(st)) return;
+    const int64_t nact = live_blocks(st, cap);
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nact * NNB) return;
     const int64_t r = t / NNB;
@@ -211,7 +230,8 @@ __global__ void k_neighbours(const int4* __restrict__ bcoord, int64_t nact, Para
     nbr[t] = hash_find(hv, pack_key(b.x + e / (R * R), b.y + (e / R) % R, b.z + e % R), P.max_probe);
 }
 
-__global__ void k_zero_grid(float4* __restrict__ gmv, float4* __restrict__ gf, int64_t nn) {
+__global__ void k_zero_grid(float4* __restrict__ gmv, float4* __restrict__ gf, int64_t nn, const DevStatus* st) {
+    if (cta_aborted(st)) return;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (int64_t)gridDim.x * blockDim.x) {
         gmv[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         gf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -225,6 +245,7 @@ __global__ void k_particle_keys(const float* __restrict__ ps, int64_t stride, in
                                 const uint32_t* __restrict__ pcode, const int* __restrict__ hvals, int B3,
                                 int by_id, uint32_t* __restrict__ key, uint32_t* __restrict__ val,
                                 DevStatus* st) {
+    if (cta_aborted(st)) return;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const uint32_t code = pcode[p];
@@ -234,7 +255,7 @@ __global__ void k_particle_keys(const float* __restrict__ ps, int64_t stride, in
     } else {
         const int r = code == 0xffffffffu ? -1 : hvals[code / (uint32_t)B3];
         if (r < 0) {
-            atomicOr(&st->map_miss, 1u);
+            raise_flag(st, &st->map_miss, 1u);
             k = 0xffffffffu;   // sorts last; k_ranges ignores it
         } else {
             k = (uint32_t)r * (uint32_t)B3 + code % (uint32_t)B3;
@@ -245,14 +266,17 @@ __global__ void k_particle_keys(const float* __restrict__ ps, int64_t stride, in
     val[q] = (uint32_t)p;
 }
 
-__global__ void k_ranges(const uint32_t* __restrict__ skey, int64_t n, int shift, int64_t nblocks,
+__global__ void k_ranges(const uint32_t* __restrict__ skey, int64_t n, int shift, int64_t cap,
                          int* __restrict__ bstart, int* __restrict__ bend, int* __restrict__ pblocks,
-                         int* __restrict__ hasp, int gen, DevStatus* st) {
+                         int* __restrict__ hasp, DevStatus* st) {
+    if (cta_aborted(st)) return;
+    const int64_t nblocks = live_blocks(st, cap);
+    const int gen = (int)st->gen;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const uint32_t r = skey[i] >> shift;
     if ((int64_t)r >= nblocks) {
-        atomicOr(&st->map_miss, 1u);
+        raise_flag(st, &st->map_miss, 1u);
         return;
     }
     const bool first = (i == 0) || ((skey[i - 1] >> shift) != r);
@@ -280,9 +304,10 @@ __device__ __forceinline__ int first_geq(const uint32_t* __restrict__ skey, int 
 // cells l and l + 32.  Output goes to the spare sort buffers.
 __global__ void __launch_bounds__(128) k_interleave(const uint32_t* __restrict__ skey, const uint32_t* __restrict__ perm,
                                                     const int* __restrict__ bstart, const int* __restrict__ bend,
-                                                    const int* __restrict__ pblocks, const DevStatus* __restrict__ stc,
+                                                    const int* __restrict__ pblocks, const DevStatus* stc,
                                                     const int* __restrict__ cs, uint32_t* __restrict__ skey2,
                                                     uint32_t* __restrict__ perm2, int* __restrict__ ccount) {
+    if (cta_aborted(stc)) return;
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * 4 + (threadIdx.x >> 5), nw = gridDim.x * 4;
     const unsigned FULL = 0xffffffffu, lt = (1u << lane) - 1u;
@@ -334,6 +359,7 @@ __global__ void __launch_bounds__(256) k_particle_bins(int64_t n, const uint32_t
                                                        const int* __restrict__ hvals, int B3, int* __restrict__ bins,
                                                        uint32_t* __restrict__ key, uint32_t* __restrict__ prank,
                                                        DevStatus* st) {
+    if (cta_aborted(st)) return;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
@@ -341,7 +367,7 @@ __global__ void __launch_bounds__(256) k_particle_bins(int64_t n, const uint32_t
     if (p < n) {
         const uint32_t code = pcode[p];
         const int r = code == 0xffffffffu ? -1 : hvals[code / (uint32_t)B3];
-        if (r < 0) atomicOr(&st->map_miss, 1u);
+        if (r < 0) raise_flag(st, &st->map_miss, 1u);
         else k = (uint32_t)r * (uint32_t)B3 + code % (uint32_t)B3;
     }
     const unsigned peers = __match_any_sync(FULL, k);
@@ -357,10 +383,19 @@ __global__ void __launch_bounds__(256) k_particle_bins(int64_t n, const uint32_t
 
 constexpr int SC_THREADS = 256, SC_ITEMS = 8, SC_TILE = SC_THREADS * SC_ITEMS;
 
-// Exclusive scan, step 1: each tile of 2048 bins scanned locally; tile totals.
-__global__ void __launch_bounds__(SC_THREADS) k_scan_tiles(const int* __restrict__ in, int64_t n,
-                                                           int* __restrict__ out, int* __restrict__ tsum) {
+// Exclusive scan of the live bins (live blocks x B3; the grid covers the
+// capacity), step 1: each tile of 2048 bins scanned locally; tile totals
+// (zero for tiles past the live bins).
+__global__ void __launch_bounds__(SC_THREADS) k_scan_tiles(const int* __restrict__ in, int64_t cap, int B3,
+                                                           const DevStatus* st, int* __restrict__ out,
+                                                           int* __restrict__ tsum) {
     __shared__ int wsum[SC_THREADS / 32];
+    if (cta_aborted(st)) return;
+    const int64_t n = live_blocks(st, cap) * B3;
+    if ((int64_t)blockIdx.x * SC_TILE >= n) {
+        if (threadIdx.x == 0) tsum[blockIdx.x] = 0;
+        return;
+    }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t base = (int64_t)blockIdx.x * SC_TILE + (int64_t)threadIdx.x * SC_ITEMS;
     int v[SC_ITEMS];
@@ -390,9 +425,10 @@ __global__ void __launch_bounds__(SC_THREADS) k_scan_tiles(const int* __restrict
 }
 
 // Step 2: exclusive scan of the tile totals (one CTA); tsum[ntiles] = total.
-__global__ void __launch_bounds__(1024) k_scan_sums(int* __restrict__ tsum, int ntiles) {
+__global__ void __launch_bounds__(1024) k_scan_sums(int* __restrict__ tsum, int ntiles, const DevStatus* st) {
     __shared__ int wsum[32];
     __shared__ int carry;
+    if (cta_aborted(st)) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
@@ -419,7 +455,10 @@ __global__ void __launch_bounds__(1024) k_scan_sums(int* __restrict__ tsum, int 
 }
 
 // Step 3: add the tile offsets; cs[n] = total.
-__global__ void k_scan_add(int* __restrict__ cs, int64_t n, const int* __restrict__ tsum, int ntiles) {
+__global__ void k_scan_add(int* __restrict__ cs, int64_t cap, int B3, const DevStatus* st,
+                           const int* __restrict__ tsum, int ntiles) {
+    if (cta_aborted(st)) return;
+    const int64_t n = live_blocks(st, cap) * B3;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) cs[i] += tsum[i / SC_TILE];
     if (i == n) cs[n] = tsum[ntiles];
@@ -427,7 +466,9 @@ __global__ void k_scan_add(int* __restrict__ cs, int64_t n, const int* __restric
 
 // Scatter into (block, cell) order.
 __global__ void k_bin_scatter(int64_t n, const uint32_t* __restrict__ key, const uint32_t* __restrict__ prank,
-                              const int* __restrict__ cs, uint32_t* __restrict__ skey, uint32_t* __restrict__ perm) {
+                              const int* __restrict__ cs, uint32_t* __restrict__ skey, uint32_t* __restrict__ perm,
+                              const DevStatus* st) {
+    if (cta_aborted(st)) return;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const uint32_t k = key[p];
@@ -438,9 +479,12 @@ __global__ void k_bin_scatter(int64_t n, const uint32_t* __restrict__ key, const
 }
 
 // Particle range and flag of every active block from the cell starts.
-__global__ void k_block_ranges(int64_t nact, int B3, const int* __restrict__ cs, int* __restrict__ bstart,
-                               int* __restrict__ bend, int* __restrict__ pblocks, int* __restrict__ hasp, int gen,
+__global__ void k_block_ranges(int64_t cap, int B3, const int* __restrict__ cs, int* __restrict__ bstart,
+                               int* __restrict__ bend, int* __restrict__ pblocks, int* __restrict__ hasp,
                                DevStatus* st) {
+    if (cta_aborted(st)) return;
+    const int64_t nact = live_blocks(st, cap);
+    const int gen = (int)st->gen;
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nact) return;
     const int s = cs[r * B3], e = cs[r * B3 + B3];
@@ -455,52 +499,57 @@ __global__ void k_block_ranges(int64_t nact, int B3, const int* __restrict__ cs,
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 }  // namespace
 
-cudaError_t launch_insert(mpm_ctx* c) {
+// Every launch below goes to c->ls and takes its sizes from capacities
+// (c->n, c->H, c->live_cap); live counts come from the status words, so the
+// same launch sequence serves any step and can be captured in a graph.
+
+cudaError_t launch_insert(mpm_ctx* c, int64_t ins_cap) {
     HashView hv{c->hkeys, c->hvals, (uint64_t)(c->H - 1)};
-    k_hash_clear<<<blocks_for(c->H, 256), 256, 0, c->st>>>(c->hkeys, c->hvals, c->H, c->dstat);
+    const unsigned gc = (unsigned)std::min<int64_t>(blocks_for(c->H, 256), 148 * 16);
+    k_hash_clear<<<gc, 256, 0, c->ls>>>(c->hkeys, c->hvals, c->H, c->dstat);
     c->launches += 2;
     const float* ps = c->ps[c->cur];
     if (c->B == 4)
-        k_insert<4><<<blocks_for(c->n, 256), 256, 0, c->st>>>(ps, c->pstride, c->n, c->P, hv, c->akey[0], c->aslot[0],
-                                                              c->block_cap, c->pcode, c->dstat);
+        k_insert<4><<<blocks_for(c->n, 256), 256, 0, c->ls>>>(ps, c->pstride, c->n, c->P, hv, c->akey[0], c->aslot[0],
+                                                              ins_cap, c->pcode, c->dstat);
     else
-        k_insert<1><<<blocks_for(c->n, 256), 256, 0, c->st>>>(ps, c->pstride, c->n, c->P, hv, c->akey[0], c->aslot[0],
-                                                              c->block_cap, c->pcode, c->dstat);
+        k_insert<1><<<blocks_for(c->n, 256), 256, 0, c->ls>>>(ps, c->pstride, c->n, c->P, hv, c->akey[0], c->aslot[0],
+                                                              ins_cap, c->pcode, c->dstat);
     return cudaGetLastError();
 }
 
 cudaError_t launch_dense_codes(mpm_ctx* c) {
-    k_status_clear<<<1, 1, 0, c->st>>>(c->dstat);
+    k_status_clear<<<1, 1, 0, c->ls>>>(c->dstat, (unsigned)c->n_dom_blocks);
     c->launches += 2;
     const float* ps = c->ps[c->cur];
     if (c->B == 4)
-        k_dense_codes<4><<<blocks_for(c->n, 256), 256, 0, c->st>>>(ps, c->pstride, c->n, c->P, c->pcode, c->dstat);
+        k_dense_codes<4><<<blocks_for(c->n, 256), 256, 0, c->ls>>>(ps, c->pstride, c->n, c->P, c->pcode, c->dstat);
     else
-        k_dense_codes<1><<<blocks_for(c->n, 256), 256, 0, c->st>>>(ps, c->pstride, c->n, c->P, c->pcode, c->dstat);
+        k_dense_codes<1><<<blocks_for(c->n, 256), 256, 0, c->ls>>>(ps, c->pstride, c->n, c->P, c->pcode, c->dstat);
     return cudaGetLastError();
 }
 
 cudaError_t launch_assign(mpm_ctx* c) {
     const int zero = c->det ? 0 : 1;
+    const int64_t cap = c->live_cap;
     if (c->dense) {
         if (zero) {
-            k_zero_grid<<<148 * 8, 256, 0, c->st>>>(c->gmv, c->gf, c->n_active * c->B3);
+            k_zero_grid<<<148 * 8, 256, 0, c->ls>>>(c->gmv, c->gf, c->n_dom_blocks * c->B3, c->dstat);
             ++c->launches;
         }
         return cudaGetLastError();
     }
-    if (c->n_active == 0) return cudaSuccess;
     const int bits = 64 - __builtin_clzll((unsigned long long)(c->n_dom_blocks > 1 ? c->n_dom_blocks - 1 : 1));
-    int sel = radix_sort_pairs(c, c->akey, c->aslot, c->n_active, nullptr, bits, c->st);
-    k_assign<<<blocks_for(c->n_active * c->B3, 256), 256, 0, c->st>>>(c->akey[sel], c->aslot[sel], c->n_active, c->P,
-                                                                      c->hvals, c->bcoord, c->gmv, c->gf,
-                                                                      counting_sort(c) ? c->bins : nullptr, c->B3, zero);
+    int sel = radix_sort_pairs(c, c->akey, c->aslot, cap, &c->dstat->n_active, bits, c->ls, &c->dstat->abort);
+    k_assign<<<blocks_for(cap * c->B3, 256), 256, 0, c->ls>>>(c->akey[sel], c->aslot[sel], cap, c->dstat, c->P,
+                                                              c->hvals, c->bcoord, c->gmv, c->gf,
+                                                              counting_sort(c) ? c->bins : nullptr, c->B3, zero);
     HashView hv{c->hkeys, c->hvals, (uint64_t)(c->H - 1)};
     const int nnb = c->B == 4 ? 8 : 27;
     if (c->B == 4)
-        k_neighbours<4><<<blocks_for(c->n_active * nnb, 256), 256, 0, c->st>>>(c->bcoord, c->n_active, c->P, hv, c->nbr);
+        k_neighbours<4><<<blocks_for(cap * nnb, 256), 256, 0, c->ls>>>(c->bcoord, cap, c->dstat, c->P, hv, c->nbr);
     else
-        k_neighbours<1><<<blocks_for(c->n_active * nnb, 256), 256, 0, c->st>>>(c->bcoord, c->n_active, c->P, hv, c->nbr);
+        k_neighbours<1><<<blocks_for(cap * nnb, 256), 256, 0, c->ls>>>(c->bcoord, cap, c->dstat, c->P, hv, c->nbr);
     c->launches += 2;
     return cudaGetLastError();
 }
@@ -509,50 +558,52 @@ bool counting_sort(const mpm_ctx* c) { return !c->dense && !c->det; }
 
 cudaError_t launch_particle_keys(mpm_ctx* c) {
     const float* ps = c->ps[c->cur];
-    const int64_t nkeys = c->n_active * c->B3;
+    const int64_t cap = c->live_cap;
+    const int64_t nkeys = cap * c->B3;
     if (counting_sort(c)) {
         // one pass: key + rank in bin; scan of the bins; scatter
-        k_particle_bins<<<blocks_for(c->n, 256), 256, 0, c->st>>>(c->n, c->pcode, c->hvals, c->B3, c->bins, c->pkey[0],
+        k_particle_bins<<<blocks_for(c->n, 256), 256, 0, c->ls>>>(c->n, c->pcode, c->hvals, c->B3, c->bins, c->pkey[0],
                                                                   c->prank, c->dstat);
         const int ntiles = (int)((nkeys + SC_TILE - 1) / SC_TILE);
-        k_scan_tiles<<<ntiles, SC_THREADS, 0, c->st>>>(c->bins, nkeys, c->cs, c->tsum);
-        k_scan_sums<<<1, 1024, 0, c->st>>>(c->tsum, ntiles);
-        k_scan_add<<<blocks_for(nkeys + 1, 256), 256, 0, c->st>>>(c->cs, nkeys, c->tsum, ntiles);
-        k_bin_scatter<<<blocks_for(c->n, 256), 256, 0, c->st>>>(c->n, c->pkey[0], c->prank, c->cs, c->pkey[1],
-                                                                c->pval[1]);
+        k_scan_tiles<<<ntiles, SC_THREADS, 0, c->ls>>>(c->bins, cap, c->B3, c->dstat, c->cs, c->tsum);
+        k_scan_sums<<<1, 1024, 0, c->ls>>>(c->tsum, ntiles, c->dstat);
+        k_scan_add<<<blocks_for(nkeys + 1, 256), 256, 0, c->ls>>>(c->cs, cap, c->B3, c->dstat, c->tsum, ntiles);
+        k_bin_scatter<<<blocks_for(c->n, 256), 256, 0, c->ls>>>(c->n, c->pkey[0], c->prank, c->cs, c->pkey[1],
+                                                                c->pval[1], c->dstat);
         c->launches += 5;
         c->sorted_sel = 1;
         return cudaGetLastError();
     }
     const int by_id = c->det ? 1 : 0;
     if (c->dense)
-        k_particle_keys<true><<<blocks_for(c->n, 256), 256, 0, c->st>>>(ps, c->pstride, c->n, c->pcode, nullptr, c->B3,
+        k_particle_keys<true><<<blocks_for(c->n, 256), 256, 0, c->ls>>>(ps, c->pstride, c->n, c->pcode, nullptr, c->B3,
                                                                        by_id, c->pkey[0], c->pval[0], c->dstat);
     else
-        k_particle_keys<false><<<blocks_for(c->n, 256), 256, 0, c->st>>>(ps, c->pstride, c->n, c->pcode, c->hvals, c->B3,
+        k_particle_keys<false><<<blocks_for(c->n, 256), 256, 0, c->ls>>>(ps, c->pstride, c->n, c->pcode, c->hvals, c->B3,
                                                                         by_id, c->pkey[0], c->pval[0], c->dstat);
     ++c->launches;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int bits = 64 - __builtin_clzll((unsigned long long)(nkeys > 1 ? nkeys - 1 : 1));
-    c->sorted_sel = radix_sort_pairs(c, c->pkey, c->pval, c->n, nullptr, bits, c->st);
+    c->sorted_sel = radix_sort_pairs(c, c->pkey, c->pval, c->n, nullptr, bits, c->ls, &c->dstat->abort);
     return cudaGetLastError();
 }
 
 cudaError_t launch_ranges(mpm_ctx* c, const uint32_t* skey) {
     const bool cnt = counting_sort(c);
+    const int64_t cap = c->live_cap;
     if (cnt) {
-        k_block_ranges<<<blocks_for(c->n_active, 256), 256, 0, c->st>>>(c->n_active, c->B3, c->cs, c->bstart, c->bend,
-                                                                        c->pblocks, c->hasp, c->gen, c->dstat);
+        k_block_ranges<<<blocks_for(cap, 256), 256, 0, c->ls>>>(cap, c->B3, c->cs, c->bstart, c->bend, c->pblocks,
+                                                                c->hasp, c->dstat);
     } else {
         const int shift = (c->B == 4) ? 6 : 0;
-        k_ranges<<<blocks_for(c->n, 256), 256, 0, c->st>>>(skey, c->n, shift, c->n_active, c->bstart, c->bend,
-                                                            c->pblocks, c->hasp, c->gen, c->dstat);
+        k_ranges<<<blocks_for(c->n, 256), 256, 0, c->ls>>>(skey, c->n, shift, cap, c->bstart, c->bend, c->pblocks,
+                                                           c->hasp, c->dstat);
     }
     ++c->launches;
     if (c->B == 4) {
         const int o = 1 - c->sorted_sel;
-        k_interleave<<<148 * 8, 128, 0, c->st>>>(skey, c->pval[c->sorted_sel], c->bstart, c->bend, c->pblocks, c->dstat,
+        k_interleave<<<148 * 8, 128, 0, c->ls>>>(skey, c->pval[c->sorted_sel], c->bstart, c->bend, c->pblocks, c->dstat,
                                                 cnt ? c->cs : nullptr, c->pkey[o], c->pval[o], c->ccount);
         c->sorted_sel = o;
         ++c->launches;

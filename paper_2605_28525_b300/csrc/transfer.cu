@@ -87,6 +87,7 @@ __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, 4) k_p2g_cells(
     __shared__ float tiles[K::WARPS][7][K::TILE];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     float(&tile)[7][K::TILE] = tiles[wid];
+    if (cta_aborted(stc)) return;
     const int nblk = (int)stc->n_pblocks;
     const int gw = blockIdx.x * K::WARPS + wid, nw = gridDim.x * K::WARPS;
     const unsigned FULL = 0xffffffffu, lt = (1u << lane) - 1u;
@@ -116,7 +117,7 @@ __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, 4) k_p2g_cells(
                     const unsigned M0 = __ballot_sync(FULL, cnt0 > k), M1 = __ballot_sync(FULL, cnt1 > k);
                     if ((M0 | M1) == 0u) break;
                     if (k >= kcap || off + __popc(M0) + __popc(M1) > kcap) {   // inconsistent counts
-                        if (lane == 0) atomicOr(&st->map_miss, 2u);
+                        if (lane == 0) raise_flag(st, &st->map_miss, 2u);
                         break;
                     }
                     if (cnt > k) {
@@ -231,10 +232,13 @@ __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, 4) k_p2g_cells(
 // step.  The result does not depend on thread timing, and the sparse and the
 // dense grid produce the same bits (absent blocks hold no particles).
 template <bool DENSE>
-__global__ void __launch_bounds__(256) k_p2g_reduce(int64_t nnodes, Params P, HashView hv,
+__global__ void __launch_bounds__(256) k_p2g_reduce(int64_t cap, const DevStatus* st, Params P, HashView hv,
                                                     const int4* __restrict__ bcoord, const float* __restrict__ tbuf,
-                                                    const int* __restrict__ hasp, int gen, float4* __restrict__ gmv,
+                                                    const int* __restrict__ hasp, float4* __restrict__ gmv,
                                                     float4* __restrict__ gf) {
+    if (cta_aborted(st)) return;
+    const int64_t nnodes = live_blocks(st, cap) * 64;
+    const int gen = (int)st->gen;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nnodes) return;
     const int r = (int)(i >> 6), l = (int)(i & 63);
@@ -269,6 +273,7 @@ __global__ void __launch_bounds__(256) k_p2g_atomic(const float* __restrict__ ps
                                                     const uint32_t* __restrict__ skey, int64_t n,
                                                     const int* __restrict__ nbr, Params P, float4* __restrict__ gmv,
                                                     float4* __restrict__ gf, DevStatus* st) {
+    if (cta_aborted(st)) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t p = perm[i];
@@ -297,7 +302,7 @@ __global__ void __launch_bounds__(256) k_p2g_atomic(const float* __restrict__ ps
             for (int c = 0; c < 3; ++c) {
                 const int rank = __ldg(&nbr[(int64_t)r * 27 + (a * 3 + b) * 3 + c]);
                 if (rank < 0) {
-                    atomicOr(&st->map_miss, 1u);
+                    raise_flag(st, &st->map_miss, 1u);
                     continue;
                 }
                 const float N = wx[a] * wy[b] * wz[c];
@@ -341,9 +346,11 @@ __device__ __forceinline__ float terrain_at(const Params& P, int ti, int tj) {
 }
 
 template <bool DENSE>
-__global__ void __launch_bounds__(256) k_grid(int64_t nnodes, int B, int S3, Params P,
+__global__ void __launch_bounds__(256) k_grid(int64_t cap, const DevStatus* st, int B, int S3, Params P,
                                               const int4* __restrict__ bcoord, const float4* __restrict__ gmv,
                                               const float4* __restrict__ gf, float4* __restrict__ gv) {
+    if (cta_aborted(st)) return;
+    const int64_t nnodes = live_blocks(st, cap) << S3;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnodes; i += (int64_t)gridDim.x * blockDim.x) {
         const int r = (int)(i >> S3), l = (int)(i & ((1 << S3) - 1));
         int bc[3];
@@ -617,6 +624,7 @@ __global__ void __launch_bounds__(256) k_g2p(const float* __restrict__ ps, float
                                               const float4* __restrict__ gv, DevStatus* st) {
     constexpr int S3 = (B == 4) ? 6 : 0;
     constexpr int NC = B * B * B;
+    if (cta_aborted(st)) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t p = perm[i];
@@ -722,7 +730,7 @@ __global__ void __launch_bounds__(256) k_g2p(const float* __restrict__ ps, float
     for (int k = 0; k < 9; ++k) fin = fin && isfinite(Fn[k]) && isfinite(Cm[k]);
     fin = fin && isfinite(xo[0]) && isfinite(xo[1]) && isfinite(xo[2]) && isfinite(tau.xx) && isfinite(tau.yy) &&
           isfinite(tau.zz) && isfinite(tau.xy) && isfinite(tau.xz) && isfinite(tau.yz);
-    if (!fin) atomicOr(&st->numeric, 1u);
+    if (!fin) raise_flag(st, &st->numeric, 1u);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         po[(PX + a) * stride + i] = xo[a];
@@ -764,6 +772,11 @@ __global__ void k_init_stress(float* __restrict__ ps, int64_t stride, int64_t n,
     ps[(PT + 5) * stride + p] = t.zz;
 }
 
+// End of a step: count it unless something raised the abort word.
+__global__ void k_step_done(DevStatus* st) {
+    if (st->abort == 0u) st->steps_done += 1u;
+}
+
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 constexpr int PERSIST = 148 * 4;   // CTAs of the block P2G (grid-stride over a device count)
@@ -775,13 +788,13 @@ cudaError_t launch_p2g(mpm_ctx* c) {
     const uint32_t* perm = c->pval[c->sorted_sel];
     HashView hv{c->hkeys, c->hvals, (uint64_t)(c->H ? c->H - 1 : 0)};
     if (c->B == 1) {
-        k_p2g_atomic<<<blocks_for(c->n, 256), 256, 0, c->st>>>(ps, c->pstride, perm, c->pkey[c->sorted_sel], c->n,
+        k_p2g_atomic<<<blocks_for(c->n, 256), 256, 0, c->ls>>>(ps, c->pstride, perm, c->pkey[c->sorted_sel], c->n,
                                                               c->nbr, c->P, c->gmv, c->gf, c->dstat);
         ++c->launches;
         return cudaGetLastError();
     }
 #define MPM_CELLS(D_, T_)                                                                                         \
-    k_p2g_cells<D_, T_><<<PERSIST, CellTileCfg::WARPS * 32, 0, c->st>>>(ps, c->pstride, perm, c->bstart, c->bend, \
+    k_p2g_cells<D_, T_><<<PERSIST, CellTileCfg::WARPS * 32, 0, c->ls>>>(ps, c->pstride, perm, c->bstart, c->bend, \
                                                                        c->pblocks, c->ccount, c->dstat, c->P,   \
                                                                        c->nbr, c->gmv, c->gf, c->tbuf, c->dstat)
     if (c->dense) {
@@ -794,24 +807,24 @@ cudaError_t launch_p2g(mpm_ctx* c) {
 #undef MPM_CELLS
     ++c->launches;
     if (c->det) {
-        const int64_t nn = c->n_active * 64;
+        const int64_t cap = c->live_cap;
         if (c->dense)
-            k_p2g_reduce<true><<<blocks_for(nn, 256), 256, 0, c->st>>>(nn, c->P, hv, c->bcoord, c->tbuf, c->hasp,
-                                                                      c->gen, c->gmv, c->gf);
+            k_p2g_reduce<true><<<blocks_for(cap * 64, 256), 256, 0, c->ls>>>(cap, c->dstat, c->P, hv, c->bcoord, c->tbuf,
+                                                                            c->hasp, c->gmv, c->gf);
         else
-            k_p2g_reduce<false><<<blocks_for(nn, 256), 256, 0, c->st>>>(nn, c->P, hv, c->bcoord, c->tbuf, c->hasp,
-                                                                       c->gen, c->gmv, c->gf);
+            k_p2g_reduce<false><<<blocks_for(cap * 64, 256), 256, 0, c->ls>>>(cap, c->dstat, c->P, hv, c->bcoord,
+                                                                             c->tbuf, c->hasp, c->gmv, c->gf);
         ++c->launches;
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_grid_update(mpm_ctx* c) {
-    const int64_t nn = c->n_active * c->B3;
+    const int64_t cap = c->live_cap;
     const int S3 = (c->B == 4) ? 6 : 0;
-    const unsigned g = (unsigned)std::min<int64_t>(blocks_for(nn, 256), 148 * 16);
-    if (c->dense) k_grid<true><<<g, 256, 0, c->st>>>(nn, c->B, S3, c->P, c->bcoord, c->gmv, c->gf, c->gv);
-    else k_grid<false><<<g, 256, 0, c->st>>>(nn, c->B, S3, c->P, c->bcoord, c->gmv, c->gf, c->gv);
+    const unsigned g = (unsigned)std::min<int64_t>(blocks_for(cap * c->B3, 256), 148 * 16);
+    if (c->dense) k_grid<true><<<g, 256, 0, c->ls>>>(cap, c->dstat, c->B, S3, c->P, c->bcoord, c->gmv, c->gf, c->gv);
+    else k_grid<false><<<g, 256, 0, c->ls>>>(cap, c->dstat, c->B, S3, c->P, c->bcoord, c->gmv, c->gf, c->gv);
     ++c->launches;
     return cudaGetLastError();
 }
@@ -823,7 +836,7 @@ cudaError_t launch_g2p(mpm_ctx* c) {
     const uint32_t* skey = c->pkey[c->sorted_sel];
     const unsigned g = blocks_for(c->n, 256);
 #define MPM_G2P(B_, D_, M_)                                                                                       \
-    k_g2p<B_, D_, M_><<<g, 256, 0, c->st>>>(ps, po, c->pstride, perm, skey, c->n, c->nbr, c->P, c->gv, c->dstat)
+    k_g2p<B_, D_, M_><<<g, 256, 0, c->ls>>>(ps, po, c->pstride, perm, skey, c->n, c->nbr, c->P, c->gv, c->dstat)
     const int mat = c->P.material;
     if (c->B == 4) {
         if (c->dense) {
@@ -843,6 +856,12 @@ cudaError_t launch_g2p(mpm_ctx* c) {
         }
     }
 #undef MPM_G2P
+    ++c->launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_done(mpm_ctx* c) {
+    k_step_done<<<1, 1, 0, c->ls>>>(c->dstat);
     ++c->launches;
     return cudaGetLastError();
 }
