@@ -104,49 +104,94 @@ def make_workload(name: str):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    """SM clocks, power and clock-event (throttle) reasons sampled through
+    NVML (the library nvidia-smi reads) from a background thread every ~2 ms
+    while the timed region runs; nvidia-smi's 200 ms loop when NVML is
+    missing.  Read-only: no setting of the GPU is touched."""
+    REASONS = (("hw_slowdown", "nvmlClocksEventReasonHwSlowdown"),
+               ("hw_thermal_slowdown", "nvmlClocksEventReasonHwThermalSlowdown"),
+               ("sw_thermal_slowdown", "nvmlClocksEventReasonSwThermalSlowdown"),
+               ("sw_power_cap", "nvmlClocksEventReasonSwPowerCap"),
+               ("hw_power_brake", "nvmlClocksEventReasonHwPowerBrakeSlowdown"))
 
-    def __init__(self, index: int):
-        self.index = index
-        self.proc = None
-        self.path = "/tmp/mpm_bench_clocks_%d_%d.csv" % (os.getpid(), index)
+    def __init__(self, device_index: int):
+        self.index = device_index
+        self.rows = []          # (sm_mhz, max_mhz, power_w, [reasons])
+        self.source = None
+        self._stop = None
+
+    def _handle(self):
+        import pynvml
+        import torch
+        pynvml.nvmlInit()
+        uuid = str(torch.cuda.get_device_properties(self.index).uuid)
+        try:
+            return pynvml.nvmlDeviceGetHandleByUUID(uuid if uuid.startswith("GPU-") else "GPU-" + uuid)
+        except Exception:
+            return pynvml.nvmlDeviceGetHandleByIndex(self.index)
+
+    def _run_nvml(self, h):
+        import pynvml
+        mx = pynvml.nvmlDeviceGetMaxClockInfo(h, pynvml.NVML_CLOCK_SM)
+        masks = [(n, getattr(pynvml, a)) for n, a in self.REASONS]
+        while not self._stop.is_set():
+            sm = pynvml.nvmlDeviceGetClockInfo(h, pynvml.NVML_CLOCK_SM)
+            r = pynvml.nvmlDeviceGetCurrentClocksEventReasons(h)
+            try:
+                pw = pynvml.nvmlDeviceGetPowerUsage(h) / 1000.0
+            except Exception:
+                pw = None
+            self.rows.append((float(sm), float(mx), pw, [n for n, m in masks if r & m]))
+            self._stop.wait(0.002)
 
     def __enter__(self):
+        import threading
+        self._stop = threading.Event()
         try:
-            self.f = open(self.path, "w")
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
-                                         stdout=self.f, stderr=subprocess.DEVNULL)
-        except OSError:
-            self.proc = None
+            h = self._handle()
+            self.source = "nvml"
+            self._thr = threading.Thread(target=self._run_nvml, args=(h,), daemon=True)
+            self._thr.start()
+        except Exception:
+            self._thr = None
+            self._smi = None
+            try:
+                self._path = "/tmp/mpm_bench_clocks_%d.csv" % os.getpid()
+                self._f = open(self._path, "w")
+                self._smi = subprocess.Popen(
+                    ["nvidia-smi", "-i", str(self.index), "--query-gpu=clocks.sm,clocks.max.sm,power.draw,"
+                     "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                     "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                     "--format=csv,noheader,nounits", "-lms", "200"], stdout=self._f, stderr=subprocess.DEVNULL)
+                self.source = "nvidia-smi"
+            except OSError:
+                self._smi = None
         return self
 
     def __exit__(self, *a):
-        if self.proc is not None:
-            self.proc.terminate()
-            self.proc.wait(timeout=10)
-            self.f.close()
+        self._stop.set()
+        if self._thr is not None:
+            self._thr.join(timeout=5)
+        elif getattr(self, "_smi", None) is not None:
+            self._smi.terminate()
+            self._smi.wait(timeout=10)
+            self._f.close()
+            for line in open(self._path):
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 7 and p[0].replace(".", "").isdigit():
+                    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+                    self.rows.append((float(p[0]), float(p[1]), None,
+                                      [names[k] for k in range(4) if p[3 + k].lower() == "active"]))
 
     def summary(self):
-        rows = []
-        try:
-            for line in open(self.path):
-                parts = [p.strip() for p in line.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
-        except OSError:
+        if not self.rows:
             return None
-        if not rows:
-            return None
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+        sm = [r[0] for r in self.rows]
+        pw = [r[2] for r in self.rows if r[2] is not None]
+        return {"sm_mhz": float(np.median(sm)), "sm_min_mhz": min(sm), "sm_max_mhz": max(r[1] for r in self.rows),
+                "reasons": sorted({n for r in self.rows for n in r[3]}),
+                "power_w_median": float(np.median(pw)) if pw else None,
+                "samples": len(self.rows), "source": self.source}
 
 
 L2_BYTES = 126 * 10 ** 6
@@ -270,7 +315,7 @@ def run_reference(args, ws, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--workload", default="column_collapse_1M")

@@ -77,8 +77,36 @@ struct CellTileCfg {
     static constexpr int WARPS = 4;
 };
 
+#ifndef MPM_P2G_MINB
+#define MPM_P2G_MINB 4
+#endif
+#ifndef MPM_G2P_MINB
+#define MPM_G2P_MINB 3     // 3 CTAs of 256 threads per SM: G2P is latency-bound, occupancy pays
+#endif
+#if MPM_G2P_MINB > 0
+#define MPM_G2P_BOUNDS __launch_bounds__(256, MPM_G2P_MINB)
+#else
+#define MPM_G2P_BOUNDS __launch_bounds__(256)
+#endif
+
+// The P2G inputs of one particle: x, v, C (scaled by h) and tau.
+struct P2GIn {
+    float x[3], v[3], hc[9], t[6];
+    __device__ __forceinline__ void load(const float* __restrict__ ps, int64_t stride, int64_t p, float h) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            x[q] = ps[(PX + q) * stride + p];
+            v[q] = ps[(PV + q) * stride + p];
+        }
+#pragma unroll
+        for (int q = 0; q < 9; ++q) hc[q] = ps[(PC + q) * stride + p] * h;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) t[q] = ps[(PT + q) * stride + p];
+    }
+};
+
 template <bool DENSE, bool DET>
-__global__ void __launch_bounds__(CellTileCfg::WARPS * 32, 4) k_p2g_cells(
+__global__ void __launch_bounds__(CellTileCfg::WARPS * 32, MPM_P2G_MINB) k_p2g_cells(
     const float* __restrict__ ps, int64_t stride, const uint32_t* __restrict__ perm,
     const int* __restrict__ bstart, const int* __restrict__ bend, const int* __restrict__ pblocks,
     const int* __restrict__ ccount, const DevStatus* __restrict__ stc, Params P, const int* __restrict__ nbr,
@@ -122,27 +150,25 @@ __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, 4) k_p2g_cells(
                     }
                     if (cnt > k) {
                         const int idx = h ? __popc(M0) + __popc(M1 & lt) : __popc(M0 & lt);
-                        const int64_t p = perm[s + off + idx];
-                        float d[3], v[3], hc[9], t[6];
+                        P2GIn in;
+                        in.load(ps, stride, perm[s + off + idx], P.h);
+                        float d[3];
 #pragma unroll
                         for (int q = 0; q < 3; ++q) {
-                            const float fx = ps[(PX + q) * stride + p] * P.inv_h;
+                            const float fx = in.x[q] * P.inv_h;
                             d[q] = fx - (float)base_index(fx);      // exact
-                            v[q] = ps[(PV + q) * stride + p];
                         }
-#pragma unroll
-                        for (int q = 0; q < 9; ++q) hc[q] = ps[(PC + q) * stride + p] * P.h;
-#pragma unroll
-                        for (int q = 0; q < 6; ++q) t[q] = ps[(PT + q) * stride + p];
+                        const float* hc = in.hc;
+                        const float* t = in.t;
                         float wx, dwx, wy[3], dwy[3], wz[3], dwz[3];
                         bspline_a(d[0], a, wx, dwx);
                         bspline3(d[1], wy, dwy);
                         bspline3(d[2], wz, dwz);
                         // momentum at node (a, b, c): v + hC (a - dx, b - dy, c - dz)
                         const float ox = (float)a - d[0];
-                        const float q0x = fmaf(hc[0], ox, v[0]) - hc[1] * d[1] - hc[2] * d[2];
-                        const float q0y = fmaf(hc[3], ox, v[1]) - hc[4] * d[1] - hc[5] * d[2];
-                        const float q0z = fmaf(hc[6], ox, v[2]) - hc[7] * d[1] - hc[8] * d[2];
+                        const float q0x = fmaf(hc[0], ox, in.v[0]) - hc[1] * d[1] - hc[2] * d[2];
+                        const float q0y = fmaf(hc[3], ox, in.v[1]) - hc[4] * d[1] - hc[5] * d[2];
+                        const float q0z = fmaf(hc[6], ox, in.v[2]) - hc[7] * d[1] - hc[8] * d[2];
 #pragma unroll
                         for (int b = 0; b < 3; ++b) {
                             // tau . grad N over c: wz (tau_r0 dwx wy + tau_r1 wx dwy) + dwz tau_r2 wx wy
@@ -211,7 +237,7 @@ __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, 4) k_p2g_cells(
             if (DENSE) rank = r + (ex * P.nb[1] + ey) * P.nb[2] + ez;
             else rank = __ldg(&nbr[(int64_t)r * 8 + (ex * 2 + ey) * 2 + ez]);
             if (rank < 0) {
-                atomicOr(&st->map_miss, 1u);
+                raise_flag(st, &st->map_miss, 1u);
                 continue;
             }
             const int l = (tx & 3) + 4 * ((ty & 3) + 4 * (tz & 3));
@@ -618,7 +644,7 @@ struct Neighbours {
 // sums are factored over z: for each (a, b) the three z-nodes are first
 // reduced with w_z, dw_z and c w_z, then scattered into v_p, B_p and L_p.
 template <int B, bool DENSE, int MAT>
-__global__ void __launch_bounds__(256) k_g2p(const float* __restrict__ ps, float* __restrict__ po, int64_t stride,
+__global__ void MPM_G2P_BOUNDS k_g2p(const float* __restrict__ ps, float* __restrict__ po, int64_t stride,
                                               const uint32_t* __restrict__ perm, const uint32_t* __restrict__ skey,
                                               int64_t n, const int* __restrict__ nbr, Params P,
                                               const float4* __restrict__ gv, DevStatus* st) {
@@ -725,11 +751,11 @@ __global__ void __launch_bounds__(256) k_g2p(const float* __restrict__ ps, float
     for (int a = 0; a < 3; ++a) xo[a] = xp[a] + P.dt * vp[a];
     const float Cm[9] = {cs * Bx[0], cs * By[0], cs * Bz[0], cs * Bx[1], cs * By[1], cs * Bz[1],
                          cs * Bx[2], cs * By[2], cs * Bz[2]};
-    bool fin = ok;
+    // one test of a sum: a NaN or an infinity in any term makes it non-finite
+    float sum = xo[0] + xo[1] + xo[2] + tau.xx + tau.yy + tau.zz + tau.xy + tau.xz + tau.yz;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) fin = fin && isfinite(Fn[k]) && isfinite(Cm[k]);
-    fin = fin && isfinite(xo[0]) && isfinite(xo[1]) && isfinite(xo[2]) && isfinite(tau.xx) && isfinite(tau.yy) &&
-          isfinite(tau.zz) && isfinite(tau.xy) && isfinite(tau.xz) && isfinite(tau.yz);
+    for (int k = 0; k < 9; ++k) sum += Fn[k] + Cm[k];
+    const bool fin = ok && isfinite(sum);
     if (!fin) raise_flag(st, &st->numeric, 1u);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
