@@ -108,51 +108,84 @@ class ClockSampler:
     NVML (the library nvidia-smi reads) from a background thread every ~2 ms
     while the timed region runs; nvidia-smi's 200 ms loop when NVML is
     missing.  Read-only: no setting of the GPU is touched."""
-    REASONS = (("hw_slowdown", "nvmlClocksEventReasonHwSlowdown"),
-               ("hw_thermal_slowdown", "nvmlClocksEventReasonHwThermalSlowdown"),
-               ("sw_thermal_slowdown", "nvmlClocksEventReasonSwThermalSlowdown"),
-               ("sw_power_cap", "nvmlClocksEventReasonSwPowerCap"),
-               ("hw_power_brake", "nvmlClocksEventReasonHwPowerBrakeSlowdown"))
-
     def __init__(self, device_index: int):
         self.index = device_index
         self.rows = []          # (sm_mhz, max_mhz, power_w, [reasons])
         self.source = None
+        self.nvml_error = None
         self._stop = None
 
-    def _handle(self):
-        import pynvml
-        import torch
-        pynvml.nvmlInit()
-        uuid = str(torch.cuda.get_device_properties(self.index).uuid)
-        try:
-            return pynvml.nvmlDeviceGetHandleByUUID(uuid if uuid.startswith("GPU-") else "GPU-" + uuid)
-        except Exception:
-            return pynvml.nvmlDeviceGetHandleByIndex(self.index)
+    class _Nvml:
+        """The few read-only NVML calls the sampler needs, through pynvml when
+        it is installed, else straight from the driver's libnvidia-ml."""
 
-    def _run_nvml(self, h):
-        import pynvml
-        mx = pynvml.nvmlDeviceGetMaxClockInfo(h, pynvml.NVML_CLOCK_SM)
-        masks = [(n, getattr(pynvml, a)) for n, a in self.REASONS]
-        while not self._stop.is_set():
-            sm = pynvml.nvmlDeviceGetClockInfo(h, pynvml.NVML_CLOCK_SM)
-            r = pynvml.nvmlDeviceGetCurrentClocksEventReasons(h)
+        def __init__(self, uuid: str, index: int):
             try:
-                pw = pynvml.nvmlDeviceGetPowerUsage(h) / 1000.0
+                import pynvml as nv
+                nv.nvmlInit()
+                try:
+                    self.h = nv.nvmlDeviceGetHandleByUUID(uuid)
+                except Exception:
+                    self.h = nv.nvmlDeviceGetHandleByIndex(index)
+                self.clock = lambda: nv.nvmlDeviceGetClockInfo(self.h, nv.NVML_CLOCK_SM)
+                self.max_clock = lambda: nv.nvmlDeviceGetMaxClockInfo(self.h, nv.NVML_CLOCK_SM)
+                self.reasons = lambda: nv.nvmlDeviceGetCurrentClocksEventReasons(self.h)
+                self.power = lambda: nv.nvmlDeviceGetPowerUsage(self.h)
+                return
+            except ImportError:
+                pass
+            import ctypes as C
+            L = C.CDLL("libnvidia-ml.so.1")
+            if L.nvmlInit_v2() != 0:
+                raise RuntimeError("nvmlInit failed")
+            h = C.c_void_p()
+            if L.nvmlDeviceGetHandleByUUID(uuid.encode(), C.byref(h)) != 0:
+                if L.nvmlDeviceGetHandleByIndex_v2(C.c_uint(index), C.byref(h)) != 0:
+                    raise RuntimeError("no NVML handle")
+            self.h = h
+
+            def q(fn, *args, kind=C.c_uint):
+                out = kind()
+                if fn(h, *args, C.byref(out)) != 0:
+                    raise RuntimeError("NVML query failed")
+                return out.value
+            self.clock = lambda: q(L.nvmlDeviceGetClockInfo, C.c_int(1))           # NVML_CLOCK_SM
+            self.max_clock = lambda: q(L.nvmlDeviceGetMaxClockInfo, C.c_int(1))
+            try:
+                rfn = L.nvmlDeviceGetCurrentClocksEventReasons
+            except AttributeError:          # older drivers: the same call under its former name
+                rfn = L.nvmlDeviceGetCurrentClocksThrottleReasons
+            self.reasons = lambda: q(rfn, kind=C.c_ulonglong)
+            self.power = lambda: q(L.nvmlDeviceGetPowerUsage)
+
+    # clock-event reason bits (nvml.h)
+    REASON_BITS = (("sw_power_cap", 0x4), ("hw_slowdown", 0x8), ("sw_thermal_slowdown", 0x20),
+                   ("hw_thermal_slowdown", 0x40), ("hw_power_brake", 0x80))
+
+    def _run_nvml(self, nv):
+        mx = nv.max_clock()
+        while not self._stop.is_set():
+            sm = nv.clock()
+            r = nv.reasons()
+            try:
+                pw = nv.power() / 1000.0
             except Exception:
                 pw = None
-            self.rows.append((float(sm), float(mx), pw, [n for n, m in masks if r & m]))
+            self.rows.append((float(sm), float(mx), pw, [n for n, m in self.REASON_BITS if r & m]))
             self._stop.wait(0.002)
 
     def __enter__(self):
         import threading
         self._stop = threading.Event()
         try:
-            h = self._handle()
+            import torch
+            uuid = str(torch.cuda.get_device_properties(self.index).uuid)
+            nv = self._Nvml(uuid if uuid.startswith("GPU-") else "GPU-" + uuid, self.index)
             self.source = "nvml"
-            self._thr = threading.Thread(target=self._run_nvml, args=(h,), daemon=True)
+            self._thr = threading.Thread(target=self._run_nvml, args=(nv,), daemon=True)
             self._thr.start()
-        except Exception:
+        except Exception as e:     # no NVML binding or device: fall back to nvidia-smi
+            self.nvml_error = "%s: %s" % (type(e).__name__, e)
             self._thr = None
             self._smi = None
             try:
@@ -176,12 +209,20 @@ class ClockSampler:
             self._smi.terminate()
             self._smi.wait(timeout=10)
             self._f.close()
-            for line in open(self._path):
-                p = [x.strip() for x in line.split(",")]
-                if len(p) >= 7 and p[0].replace(".", "").isdigit():
-                    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-                    self.rows.append((float(p[0]), float(p[1]), None,
-                                      [names[k] for k in range(4) if p[3 + k].lower() == "active"]))
+            self.rows.extend(self.parse_smi(open(self._path)))
+
+    @staticmethod
+    def parse_smi(lines):
+        """Rows of the nvidia-smi query above: sm, max sm, power, then four
+        reason columns ("Active" / "Not Active")."""
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
+        for line in lines:
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 7 and p[0].replace(".", "").isdigit():
+                pw = float(p[2]) if p[2].replace(".", "").isdigit() else None
+                rows.append((float(p[0]), float(p[1]), pw, [names[k] for k in range(4) if p[3 + k].lower() == "active"]))
+        return rows
 
     def summary(self):
         if not self.rows:
@@ -191,7 +232,8 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)), "sm_min_mhz": min(sm), "sm_max_mhz": max(r[1] for r in self.rows),
                 "reasons": sorted({n for r in self.rows for n in r[3]}),
                 "power_w_median": float(np.median(pw)) if pw else None,
-                "samples": len(self.rows), "source": self.source}
+                "samples": len(self.rows), "source": self.source,
+                **({"nvml_error": self.nvml_error} if self.nvml_error else {})}
 
 
 L2_BYTES = 126 * 10 ** 6

@@ -705,6 +705,15 @@ static mpm_status create_impl(const mpm_config* cfg, int64_t n, const float* x, 
         c->block_cap = c->n_dom_blocks;
         CK(radix_reserve(c, std::max<int64_t>(n, c->block_cap)));
     } else {
+        // bit mask over the box's blocks for the ranking, unless it would
+        // exceed 64 MiB (then the keys are radix-sorted)
+        const int64_t words = (c->n_dom_blocks + 31) / 32;
+        if (words <= ((int64_t)1 << 24)) {
+            c->bwords = words;
+            CK(dalloc(c, (void**)&c->bmask, sizeof(uint32_t) * words));
+            CK(dalloc(c, (void**)&c->bpre, sizeof(int) * (words + 1)));
+            CK(dalloc(c, (void**)&c->btsum, sizeof(int) * (words / 2048 + 2)));
+        }
         int64_t cap = cfg->block_capacity ? cfg->block_capacity : std::max<int64_t>(1024, n / 32);
         int64_t H = cfg->hash_capacity ? cfg->hash_capacity : next_pow2(2 * cap);
         CK(alloc_hash(c, H, cap));

@@ -206,6 +206,10 @@ struct mpm_ctx {
     uint32_t* akey[2] = {nullptr, nullptr};
     uint32_t* aslot[2] = {nullptr, nullptr};
     int4* bcoord = nullptr;      // per Phi: block coordinates
+    uint32_t* bmask = nullptr;   // bit per block of the box: set when the insert claims its key
+    int* bpre = nullptr;         // exclusive scan of the words' bit counts (+ total): Phi = rank
+    int* btsum = nullptr;        // scan tile totals
+    int64_t bwords = 0;          // words of bmask (0: the block keys are radix-sorted instead)
     int64_t block_cap = 0;
     int64_t live_cap = 0;        // active blocks every per-step array can hold (<= block_cap)
     int64_t n_dom_blocks = 0;

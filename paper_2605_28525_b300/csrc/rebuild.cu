@@ -11,9 +11,14 @@
 //                     n_probe, overflow flag on failure or capacity excess.
 //   (host)            Alg. 7: on overflow double H (and the list capacity)
 //                     and insert again.
-//   k_assign          Phi(b) = rank of b in ascending Eq.-(key) order, written
-//                     to the table value of its slot; block coordinates per
+//   k_assign_bits     Phi(b) = rank of b in ascending Eq.-(key) order: the
+//                     insert also sets b's bit in a bit mask over the blocks
+//                     of the box, and the rank is the bit count below it (a
+//                     scan of the words' counts, then a popcount); written to
+//                     the table value of its slot; block coordinates per
 //                     Phi; the block's grid nodes are zeroed for P2G.
+//                     (k_assign: the same from a radix sort of the keys, for
+//                     boxes whose mask would be too large.)
 //   k_particle_keys   sort key (Phi(b(base)), l(base)) per particle.
 //   k_ranges          particle range of every block that holds particles and
 //                     the list of such blocks.
@@ -33,7 +38,7 @@ namespace {
 // test `abort` itself, since its own overflow would stop its later CTAs and
 // the block count the host regrows from would come out short.
 __global__ void k_hash_clear(unsigned long long* __restrict__ keys, int* __restrict__ vals, int64_t H,
-                             DevStatus* st) {
+                             uint32_t* __restrict__ bmask, int64_t bwords, DevStatus* st) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool ab = *((volatile unsigned int*)&st->abort) != 0u;
     if (i == 0) st->go = ab ? 0u : 1u;
@@ -42,6 +47,7 @@ __global__ void k_hash_clear(unsigned long long* __restrict__ keys, int* __restr
         keys[j] = EMPTY_KEY;
         vals[j] = -1;
     }
+    for (int64_t j = i; j < bwords; j += (int64_t)gridDim.x * blockDim.x) bmask[j] = 0u;
     if (i == 0) {
         st->n_active = 0;
         st->n_pblocks = 0;
@@ -63,7 +69,7 @@ __global__ void k_status_clear(DevStatus* st, unsigned int n_dom_blocks) {
 // were all taken by other keys (overflow).
 __device__ int hash_insert(const HashView& hv, uint64_t key, uint32_t rkey, int max_probe,
                            uint32_t* __restrict__ akey, uint32_t* __restrict__ aslot, int64_t cap,
-                           DevStatus* st) {
+                           uint32_t* __restrict__ bmask, DevStatus* st) {
     uint64_t s = mix64(key) & hv.mask;
     for (int r = 0; r < max_probe; ++r) {
         unsigned long long cur = *((volatile unsigned long long*)&hv.keys[s]);
@@ -71,6 +77,7 @@ __device__ int hash_insert(const HashView& hv, uint64_t key, uint32_t rkey, int 
         if (cur == EMPTY_KEY) {
             unsigned long long old = atomicCAS(&hv.keys[s], EMPTY_KEY, (unsigned long long)key);
             if (old == EMPTY_KEY) {
+                if (bmask) atomicOr(&bmask[rkey >> 5], 1u << (rkey & 31u));
                 unsigned idx = atomicAdd(&st->n_active, 1u);
                 if ((int64_t)idx < cap) {
                     akey[idx] = rkey;
@@ -118,7 +125,8 @@ template <int B>
 __global__ void __launch_bounds__(256) k_insert(const float* __restrict__ ps, int64_t stride, int64_t n,
                                                 Params P, HashView hv, uint32_t* __restrict__ akey,
                                                 uint32_t* __restrict__ aslot, int64_t cap,
-                                                uint32_t* __restrict__ pcode, DevStatus* st) {
+                                                uint32_t* __restrict__ bmask, uint32_t* __restrict__ pcode,
+                                                DevStatus* st) {
     constexpr int S = (B == 4) ? 2 : 0;
     constexpr int R = (B == 4) ? 2 : 3;   // blocks a stencil can span per axis
     constexpr int NJ = R * R * R;
@@ -164,7 +172,7 @@ __global__ void __launch_bounds__(256) k_insert(const float* __restrict__ ps, in
             const int j = __ffs(m) - 1;
             const int bi = b0[0] + j / (R * R), bj = b0[1] + (j / R) % R, bk = b0[2] + j % R;
             const int slot = hash_insert(hv, pack_key(bi, bj, bk), rel_key(P, bi, bj, bk), P.max_probe, akey, aslot,
-                                         cap, st);
+                                         cap, bmask, st);
             if (j == 0) myslot = slot;   // bit 0 (the base block) is taken by rank 0 = the leader
         }
     }
@@ -211,6 +219,36 @@ __global__ void k_assign(const uint32_t* __restrict__ skey, const uint32_t* __re
         gf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     if (bins) bins[i] = 0;   // counting-sort bins: one per (block, cell) = one per node
+}
+
+// Phi from the block bit mask: the rank of a key is the number of set bits
+// below it.  Thread i handles node i % B3 of the i / B3-th inserted block.
+__global__ void k_assign_bits(const uint32_t* __restrict__ akey, const uint32_t* __restrict__ aslot, int64_t cap,
+                              const DevStatus* st, Params P, const uint32_t* __restrict__ bmask,
+                              const int* __restrict__ bpre, int* __restrict__ hvals, int4* __restrict__ bcoord,
+                              float4* __restrict__ gmv, float4* __restrict__ gf, int* __restrict__ bins, int B3,
+                              int zero_grid) {
+    if (cta_aborted(st)) return;
+    const int64_t nact = live_blocks(st, cap);
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nact * B3) return;
+    const int64_t q = i / B3;
+    const int l = (int)(i % B3);
+    const uint32_t key = akey[q];
+    const uint32_t w = key >> 5;
+    const int64_t r = (int64_t)bpre[w] + __popc(bmask[w] & ((1u << (key & 31u)) - 1u));
+    if (l == 0) {
+        hvals[aslot[q]] = (int)r;
+        int bi, bj, bk;
+        rel_decode(P, key, bi, bj, bk);
+        bcoord[r] = make_int4(bi, bj, bk, 0);
+    }
+    const int64_t node = r * B3 + l;
+    if (zero_grid) {
+        gmv[node] = make_float4(0.f, 0.f, 0.f, 0.f);
+        gf[node] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (bins) bins[node] = 0;
 }
 
 // Phi of the blocks b + {0..R-1}^3 of every active block (runs after
@@ -464,6 +502,50 @@ __global__ void k_scan_add(int* __restrict__ cs, int64_t cap, int B3, const DevS
     if (i == n) cs[n] = tsum[ntiles];
 }
 
+// Exclusive scan of the bit counts of the block mask's words, step 1 (the
+// scan's steps 2 and 3 are k_scan_sums and k_scan_add_n).
+__global__ void __launch_bounds__(SC_THREADS) k_bits_scan_tiles(const uint32_t* __restrict__ bmask, int64_t n,
+                                                                const DevStatus* st, int* __restrict__ out,
+                                                                int* __restrict__ tsum) {
+    __shared__ int wsum[SC_THREADS / 32];
+    if (cta_aborted(st)) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * SC_TILE + (int64_t)threadIdx.x * SC_ITEMS;
+    int v[SC_ITEMS];
+    int tot = 0;
+#pragma unroll
+    for (int j = 0; j < SC_ITEMS; ++j) {
+        v[j] = base + j < n ? __popc(bmask[base + j]) : 0;
+        tot += v[j];
+    }
+    int x = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    int pre = 0;
+    for (int k = 0; k < w; ++k) pre += wsum[k];
+    int run = pre + x - tot;
+#pragma unroll
+    for (int j = 0; j < SC_ITEMS; ++j) {
+        if (base + j < n) out[base + j] = run;
+        run += v[j];
+    }
+    if (threadIdx.x == SC_THREADS - 1) tsum[blockIdx.x] = pre + x;
+}
+
+// Step 3 for a fixed count n: add the tile offsets; cs[n] = total.
+__global__ void k_scan_add_n(int* __restrict__ cs, int64_t n, const DevStatus* st, const int* __restrict__ tsum,
+                             int ntiles) {
+    if (cta_aborted(st)) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) cs[i] += tsum[i / SC_TILE];
+    if (i == n) cs[n] = tsum[ntiles];
+}
+
 // Scatter into (block, cell) order.
 __global__ void k_bin_scatter(int64_t n, const uint32_t* __restrict__ key, const uint32_t* __restrict__ prank,
                               const int* __restrict__ cs, uint32_t* __restrict__ skey, uint32_t* __restrict__ perm,
@@ -506,15 +588,15 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 cudaError_t launch_insert(mpm_ctx* c, int64_t ins_cap) {
     HashView hv{c->hkeys, c->hvals, (uint64_t)(c->H - 1)};
     const unsigned gc = (unsigned)std::min<int64_t>(blocks_for(c->H, 256), 148 * 16);
-    k_hash_clear<<<gc, 256, 0, c->ls>>>(c->hkeys, c->hvals, c->H, c->dstat);
+    k_hash_clear<<<gc, 256, 0, c->ls>>>(c->hkeys, c->hvals, c->H, c->bmask, c->bwords, c->dstat);
     c->launches += 2;
     const float* ps = c->ps[c->cur];
     if (c->B == 4)
         k_insert<4><<<blocks_for(c->n, 256), 256, 0, c->ls>>>(ps, c->pstride, c->n, c->P, hv, c->akey[0], c->aslot[0],
-                                                              ins_cap, c->pcode, c->dstat);
+                                                              ins_cap, c->bmask, c->pcode, c->dstat);
     else
         k_insert<1><<<blocks_for(c->n, 256), 256, 0, c->ls>>>(ps, c->pstride, c->n, c->P, hv, c->akey[0], c->aslot[0],
-                                                              ins_cap, c->pcode, c->dstat);
+                                                              ins_cap, c->bmask, c->pcode, c->dstat);
     return cudaGetLastError();
 }
 
@@ -539,18 +621,31 @@ cudaError_t launch_assign(mpm_ctx* c) {
         }
         return cudaGetLastError();
     }
-    const int bits = 64 - __builtin_clzll((unsigned long long)(c->n_dom_blocks > 1 ? c->n_dom_blocks - 1 : 1));
-    int sel = radix_sort_pairs(c, c->akey, c->aslot, cap, &c->dstat->n_active, bits, c->ls, &c->dstat->abort);
-    k_assign<<<blocks_for(cap * c->B3, 256), 256, 0, c->ls>>>(c->akey[sel], c->aslot[sel], cap, c->dstat, c->P,
-                                                              c->hvals, c->bcoord, c->gmv, c->gf,
-                                                              counting_sort(c) ? c->bins : nullptr, c->B3, zero);
+    int* bins = counting_sort(c) ? c->bins : nullptr;
+    if (c->bmask) {
+        const int ntiles = (int)((c->bwords + SC_TILE - 1) / SC_TILE);
+        k_bits_scan_tiles<<<ntiles, SC_THREADS, 0, c->ls>>>(c->bmask, c->bwords, c->dstat, c->bpre, c->btsum);
+        k_scan_sums<<<1, 1024, 0, c->ls>>>(c->btsum, ntiles, c->dstat);
+        k_scan_add_n<<<blocks_for(c->bwords + 1, 256), 256, 0, c->ls>>>(c->bpre, c->bwords, c->dstat, c->btsum, ntiles);
+        k_assign_bits<<<blocks_for(cap * c->B3, 256), 256, 0, c->ls>>>(c->akey[0], c->aslot[0], cap, c->dstat, c->P,
+                                                                       c->bmask, c->bpre, c->hvals, c->bcoord, c->gmv,
+                                                                       c->gf, bins, c->B3, zero);
+        c->launches += 4;
+    } else {
+        const int bits = 64 - __builtin_clzll((unsigned long long)(c->n_dom_blocks > 1 ? c->n_dom_blocks - 1 : 1));
+        int sel = radix_sort_pairs(c, c->akey, c->aslot, cap, &c->dstat->n_active, bits, c->ls, &c->dstat->abort);
+        k_assign<<<blocks_for(cap * c->B3, 256), 256, 0, c->ls>>>(c->akey[sel], c->aslot[sel], cap, c->dstat, c->P,
+                                                                  c->hvals, c->bcoord, c->gmv, c->gf, bins, c->B3,
+                                                                  zero);
+        ++c->launches;
+    }
     HashView hv{c->hkeys, c->hvals, (uint64_t)(c->H - 1)};
     const int nnb = c->B == 4 ? 8 : 27;
     if (c->B == 4)
         k_neighbours<4><<<blocks_for(cap * nnb, 256), 256, 0, c->ls>>>(c->bcoord, cap, c->dstat, c->P, hv, c->nbr);
     else
         k_neighbours<1><<<blocks_for(cap * nnb, 256), 256, 0, c->ls>>>(c->bcoord, cap, c->dstat, c->P, hv, c->nbr);
-    c->launches += 2;
+    ++c->launches;
     return cudaGetLastError();
 }
 

@@ -56,8 +56,10 @@ def test_bench_traffic_lookup_and_clock_summary(tmp_path):
     import bench
     assert bench.measured_traffic("no_such_workload", "p2g") is None
     s = bench.ClockSampler(0)
-    s.path = str(tmp_path / "c.csv")
-    open(s.path, "w").write("0, 1900, 2032, 700, 0x0, Not Active, Not Active, Not Active, Active\n"
-                            "0, 1950, 2032, 710, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+    s.source = "nvidia-smi"
+    s.rows = bench.ClockSampler.parse_smi(["1900, 2032, 700.5, Not Active, Not Active, Not Active, Active",
+                                           "1950, 2032, 710.0, Not Active, Not Active, Not Active, Not Active",
+                                           "garbage line"])
     out = s.summary()
     assert out["sm_mhz"] == 1925.0 and out["sm_max_mhz"] == 2032.0 and out["reasons"] == ["sw_power_cap"]
+    assert out["samples"] == 2 and abs(out["power_w_median"] - 705.25) < 1e-9
