@@ -72,7 +72,7 @@ __device__ __forceinline__ int block_rank(const Params& P, const HashView& hv, i
 // nodes with float4 global atomics.
 struct CellTileCfg {
     static constexpr int T = 6;                    // tile edge (B + 2 with B = 4)
-    static constexpr int SY = 8, SZ = 68;          // strides: conflict-free for one half's 32 cells
+    static constexpr int SY = 8, SZ = 52;          // strides: conflict-free for one half's 32 cells
     static constexpr int TILE = (T - 1) * (SZ + SY) + T;
     static constexpr int WARPS = 4;
 };
@@ -104,6 +104,50 @@ struct P2GIn {
         for (int q = 0; q < 6; ++q) t[q] = ps[(PT + q) * stride + p];
     }
 };
+
+// Adds one particle's contributions to the 9 nodes (a, 0..2, 0..2) of its
+// stencil: 7 channels (m, m v, f) per node, in units of m_p and -V0/h.
+__device__ __forceinline__ void p2g_accumulate(const Params& P, const P2GIn& in, int a, float (&acc)[3][3][7]) {
+    float d[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const float fx = in.x[q] * P.inv_h;
+        d[q] = fx - (float)base_index(fx);      // exact
+    }
+    const float* hc = in.hc;
+    const float* t = in.t;
+    float wx, dwx, wy[3], dwy[3], wz[3], dwz[3];
+    bspline_a(d[0], a, wx, dwx);
+    bspline3(d[1], wy, dwy);
+    bspline3(d[2], wz, dwz);
+    // momentum at node (a, b, c): v + hC (a - dx, b - dy, c - dz)
+    const float ox = (float)a - d[0];
+    const float q0x = fmaf(hc[0], ox, in.v[0]) - hc[1] * d[1] - hc[2] * d[2];
+    const float q0y = fmaf(hc[3], ox, in.v[1]) - hc[4] * d[1] - hc[5] * d[2];
+    const float q0z = fmaf(hc[6], ox, in.v[2]) - hc[7] * d[1] - hc[8] * d[2];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        // tau . grad N over c: wz (tau_r0 dwx wy + tau_r1 wx dwy) + dwz tau_r2 wx wy
+        const float Pw = wx * wy[b], Gx = dwx * wy[b], Gy = wx * dwy[b];
+        const float A0 = t[0] * Gx + t[1] * Gy, A1 = t[1] * Gx + t[3] * Gy, A2 = t[2] * Gx + t[4] * Gy;
+        const float B0 = t[2] * Pw, B1 = t[4] * Pw, B2 = t[5] * Pw;
+        const float qbx = fmaf(hc[1], (float)b, q0x), qby = fmaf(hc[4], (float)b, q0y),
+                    qbz = fmaf(hc[7], (float)b, q0z);
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) {
+            const float N = Pw * wz[cc];
+            const float mx = fmaf(hc[2], (float)cc, qbx), my = fmaf(hc[5], (float)cc, qby),
+                        mz = fmaf(hc[8], (float)cc, qbz);
+            acc[b][cc][0] += N;
+            acc[b][cc][1] = fmaf(N, mx, acc[b][cc][1]);
+            acc[b][cc][2] = fmaf(N, my, acc[b][cc][2]);
+            acc[b][cc][3] = fmaf(N, mz, acc[b][cc][3]);
+            acc[b][cc][4] = fmaf(wz[cc], A0, fmaf(dwz[cc], B0, acc[b][cc][4]));
+            acc[b][cc][5] = fmaf(wz[cc], A1, fmaf(dwz[cc], B1, acc[b][cc][5]));
+            acc[b][cc][6] = fmaf(wz[cc], A2, fmaf(dwz[cc], B2, acc[b][cc][6]));
+        }
+    }
+}
 
 template <bool DENSE, bool DET>
 __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, MPM_P2G_MINB) k_p2g_cells(
@@ -152,46 +196,7 @@ __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, MPM_P2G_MINB) k_p2g_c
                         const int idx = h ? __popc(M0) + __popc(M1 & lt) : __popc(M0 & lt);
                         P2GIn in;
                         in.load(ps, stride, perm[s + off + idx], P.h);
-                        float d[3];
-#pragma unroll
-                        for (int q = 0; q < 3; ++q) {
-                            const float fx = in.x[q] * P.inv_h;
-                            d[q] = fx - (float)base_index(fx);      // exact
-                        }
-                        const float* hc = in.hc;
-                        const float* t = in.t;
-                        float wx, dwx, wy[3], dwy[3], wz[3], dwz[3];
-                        bspline_a(d[0], a, wx, dwx);
-                        bspline3(d[1], wy, dwy);
-                        bspline3(d[2], wz, dwz);
-                        // momentum at node (a, b, c): v + hC (a - dx, b - dy, c - dz)
-                        const float ox = (float)a - d[0];
-                        const float q0x = fmaf(hc[0], ox, in.v[0]) - hc[1] * d[1] - hc[2] * d[2];
-                        const float q0y = fmaf(hc[3], ox, in.v[1]) - hc[4] * d[1] - hc[5] * d[2];
-                        const float q0z = fmaf(hc[6], ox, in.v[2]) - hc[7] * d[1] - hc[8] * d[2];
-#pragma unroll
-                        for (int b = 0; b < 3; ++b) {
-                            // tau . grad N over c: wz (tau_r0 dwx wy + tau_r1 wx dwy) + dwz tau_r2 wx wy
-                            const float Pw = wx * wy[b], Gx = dwx * wy[b], Gy = wx * dwy[b];
-                            const float A0 = t[0] * Gx + t[1] * Gy, A1 = t[1] * Gx + t[3] * Gy,
-                                        A2 = t[2] * Gx + t[4] * Gy;
-                            const float B0 = t[2] * Pw, B1 = t[4] * Pw, B2 = t[5] * Pw;
-                            const float qbx = fmaf(hc[1], (float)b, q0x), qby = fmaf(hc[4], (float)b, q0y),
-                                        qbz = fmaf(hc[7], (float)b, q0z);
-#pragma unroll
-                            for (int cc = 0; cc < 3; ++cc) {
-                                const float N = Pw * wz[cc];
-                                const float mx = fmaf(hc[2], (float)cc, qbx), my = fmaf(hc[5], (float)cc, qby),
-                                            mz = fmaf(hc[8], (float)cc, qbz);
-                                acc[b][cc][0] += N;
-                                acc[b][cc][1] = fmaf(N, mx, acc[b][cc][1]);
-                                acc[b][cc][2] = fmaf(N, my, acc[b][cc][2]);
-                                acc[b][cc][3] = fmaf(N, mz, acc[b][cc][3]);
-                                acc[b][cc][4] = fmaf(wz[cc], A0, fmaf(dwz[cc], B0, acc[b][cc][4]));
-                                acc[b][cc][5] = fmaf(wz[cc], A1, fmaf(dwz[cc], B1, acc[b][cc][5]));
-                                acc[b][cc][6] = fmaf(wz[cc], A2, fmaf(dwz[cc], B2, acc[b][cc][6]));
-                            }
-                        }
+                        p2g_accumulate(P, in, a, acc);
                     }
                     off += __popc(M0) + __popc(M1);
                 }
@@ -805,7 +810,7 @@ __global__ void k_step_done(DevStatus* st) {
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-constexpr int PERSIST = 148 * 4;   // CTAs of the block P2G (grid-stride over a device count)
+constexpr int PERSIST = 148 * MPM_P2G_MINB;   // CTAs of the block P2G (grid-stride over a device count)
 
 }  // namespace
 
