@@ -49,7 +49,8 @@ struct DevStatus {
     unsigned int steps_done;     // steps completed without error since the host cleared it
     unsigned int gen;            // step generation (block "holds particles" marks)
     unsigned int go;             // the running step's insert may proceed (written by the table clear)
-    unsigned int pad[6];
+    unsigned int work;           // next P2G work unit (dynamic scheduling; zeroed by the table clear)
+    unsigned int pad[5];
 };
 
 __device__ __forceinline__ void raise_flag(DevStatus* s, unsigned int* word, unsigned int bits) {

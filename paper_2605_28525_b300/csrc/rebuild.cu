@@ -51,6 +51,7 @@ __global__ void k_hash_clear(unsigned long long* __restrict__ keys, int* __restr
     if (i == 0) {
         st->n_active = 0;
         st->n_pblocks = 0;
+        st->work = 0;
         st->gen += 1u;
     }
 }
@@ -62,6 +63,7 @@ __global__ void k_status_clear(DevStatus* st, unsigned int n_dom_blocks) {
     if (ab) return;
     st->n_active = n_dom_blocks;
     st->n_pblocks = 0;
+    st->work = 0;
     st->gen += 1u;
 }
 

@@ -11,7 +11,8 @@
 //      which also stores the Kirchhoff stress tau for the next P2G.
 //
 // Two P2G variants:
-//   k_p2g_cells   one warp per block that holds particles, lane = cell, with
+//   k_p2g_cells   one warp per half block (32 cells) that holds particles,
+//                 handed out dynamically, lane = cell, with
 //                 the block's particles in k-major order; register sums per
 //                 (cell, x-offset) and a warp-private shared tile updated
 //                 without atomics, flushed with float4 global atomics into the
@@ -156,25 +157,36 @@ __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, MPM_P2G_MINB) k_p2g_c
     const int* __restrict__ ccount, const DevStatus* __restrict__ stc, Params P, const int* __restrict__ nbr,
     float4* __restrict__ gmv, float4* __restrict__ gf, float* __restrict__ tbuf, DevStatus* st) {
     using K = CellTileCfg;
+    // Work unit: a half block (32 cells, tile z-layers 2h..2h+3) in the fast
+    // mode, a whole block in the deterministic mode (its tile goes to tbuf as
+    // one piece).  Units are handed out dynamically.
+    constexpr int HU = DET ? 1 : 2;
+    constexpr int TZ = DET ? K::T : 4;
     __shared__ float tiles[K::WARPS][7][K::TILE];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     float(&tile)[7][K::TILE] = tiles[wid];
     if (cta_aborted(stc)) return;
-    const int nblk = (int)stc->n_pblocks;
-    const int gw = blockIdx.x * K::WARPS + wid, nw = gridDim.x * K::WARPS;
+    const int nunits = (int)stc->n_pblocks * HU;
     const unsigned FULL = 0xffffffffu, lt = (1u << lane) - 1u;
 
     for (int i = lane; i < 7 * K::TILE; i += 32) (&tile[0][0])[i] = 0.f;
     __syncwarp();
 
-    for (int kb = gw; kb < nblk; kb += nw) {
-        const int r = pblocks[kb];
+    for (;;) {
+        int u = 0;
+        if (lane == 0) u = (int)atomicAdd(&st->work, 1u);
+        u = __shfl_sync(FULL, u, 0);
+        if (u >= nunits) break;
+        const int r = pblocks[u / HU];
+        const int h0 = DET ? 0 : u % HU, h1 = DET ? 2 : h0 + 1;
+        const int zoff = DET ? 0 : 2 * h0;              // block z-layer of the tile's layer 0
         const int s = bstart[r], kcap = bend[r] - s;   // no cell holds more than the block's particles
         const int cnt0 = ccount[(int64_t)r * 64 + lane], cnt1 = ccount[(int64_t)r * 64 + 32 + lane];
+        if (!DET && __ballot_sync(FULL, (h0 ? cnt1 : cnt0) > 0) == 0u) continue;   // empty half
 #pragma unroll 1
-        for (int h = 0; h < 2; ++h) {
+        for (int h = h0; h < h1; ++h) {
             const int cnt = h ? cnt1 : cnt0;
-            const int cx = lane & 3, cy = (lane >> 2) & 3, cz = 2 * h + (lane >> 4);
+            const int cx = lane & 3, cy = (lane >> 2) & 3, cz = 2 * h + (lane >> 4) - zoff;
 #pragma unroll 1
             for (int a = 0; a < 3; ++a) {
                 float acc[3][3][7];
@@ -184,6 +196,8 @@ __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, MPM_P2G_MINB) k_p2g_c
                     for (int cc = 0; cc < 3; ++cc)
 #pragma unroll
                         for (int k = 0; k < 7; ++k) acc[b][cc][k] = 0.f;
+                // round k: the k-th particle of every cell (both halves, in
+                // the block's k-major order)
                 int off = 0;
                 for (int k = 0;; ++k) {
                     const unsigned M0 = __ballot_sync(FULL, cnt0 > k), M1 = __ballot_sync(FULL, cnt1 > k);
@@ -219,9 +233,9 @@ __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, MPM_P2G_MINB) k_p2g_c
         // flush the tile: deterministic mode stores it for k_p2g_reduce, the
         // fast mode adds it to the active nodes of this block and its neighbours
         const float fs = -P.V0 * P.inv_h;
-        for (int t = lane; t < K::T * K::T * K::T; t += 32) {
-            const int tx = t % K::T, ty = (t / K::T) % K::T, tz = t / (K::T * K::T);
-            const int ti = tx + K::SY * ty + K::SZ * tz;
+        for (int t = lane; t < K::T * K::T * TZ; t += 32) {
+            const int tx = t % K::T, ty = (t / K::T) % K::T, tzl = t / (K::T * K::T);
+            const int ti = tx + K::SY * ty + K::SZ * tzl;
             float v[7];
 #pragma unroll
             for (int k = 0; k < 7; ++k) {
@@ -237,6 +251,7 @@ __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, MPM_P2G_MINB) k_p2g_c
             if (v[0] == 0.f && v[1] == 0.f && v[2] == 0.f && v[3] == 0.f && v[4] == 0.f && v[5] == 0.f &&
                 v[6] == 0.f)
                 continue;
+            const int tz = tzl + zoff;
             const int ex = tx >> 2, ey = ty >> 2, ez = tz >> 2;
             int rank;
             if (DENSE) rank = r + (ex * P.nb[1] + ey) * P.nb[2] + ez;
