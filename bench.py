@@ -100,6 +100,8 @@ def make_workload(name: str):
         return W.landslide()
     if name == "elastic_cube_32k":
         return W.elastic_cube()
+    if name == "column_ensemble_64":
+        return W.column_ensemble()
     raise SystemExit("unknown workload %s" % name)
 
 
@@ -332,10 +334,14 @@ def run_reference(args, ws, rank):
     if rank != 0:
         return
     wl = make_workload(args.workload)
+    if wl.scenario_counts is not None:          # the oracle runs one scenario of an ensemble
+        from paper_2605_28525_b300 import workloads as W
+        wl = W.ensemble_member(wl, 0)
     import oracle
     o_args = dict(lo=wl.lo, hi=wl.hi, h=wl.dx, dt=wl.dt, g=wl.gravity, B=wl.block_size, material=wl.material,
                   E=wl.E, nu=wl.nu, rho=wl.rho, phi_deg=wl.phi_deg, ppc=wl.ppc, floor_kind=wl.floor_kind,
-                  floor_z=wl.floor_z, floor_mu=wl.floor_mu, wall_layers=wl.wall_layers)
+                  floor_z=wl.floor_z, floor_mu=wl.floor_mu, wall_layers=wl.wall_layers,
+                  terrain=None if wl.terrain is None else wl.terrain.astype(np.float64), terrain_mu=wl.terrain_mu)
     o = oracle.Oracle(**o_args)
     x, v, Cm, F = o.run(wl.x, wl.v, None, None, wl.phi, nsteps=args.warmup)
     t0 = time.perf_counter()
@@ -428,7 +434,7 @@ def main():
     sim.close()
 
     dense = None
-    if not args.no_dense:
+    if not args.no_dense and wl.scenario_counts is None:   # ensembles run on the sparse grid only
         dsim = mpm.Simulation.from_workload(wl, flags=mpm.DENSE_GRID, stream=stream, device_inputs=True)
         for _ in range(3):
             dsim.step(1)
@@ -441,10 +447,12 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        cv, cdt = cpu_baseline(wl, args.cpu_steps)
+        from paper_2605_28525_b300 import workloads as W
+        cwl = wl if wl.scenario_counts is None else W.ensemble_member(wl, 0)   # the oracle runs one scenario
+        cv, cdt = cpu_baseline(cwl, args.cpu_steps)
         cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "%d full FP64 oracle steps of %s (%d particles, dense %s node grid), %.1f s" % (
-                   args.cpu_steps, wl.name, wl.n, "x".join(str(wl.hi[a] - wl.lo[a] + 1) for a in range(3)), cdt)}
+                   args.cpu_steps, cwl.name, cwl.n, "x".join(str(cwl.hi[a] - cwl.lo[a] + 1) for a in range(3)), cdt)}
 
     if rank == 0:
         line = {

@@ -121,6 +121,8 @@ typedef struct mpm_stats {
     int64_t kernel_launches;     /* CUDA kernels this context has launched */
     int32_t flags;
     int32_t block_size;
+    int32_t n_scenarios;         /* 1, or the scenarios of an ensemble context */
+    int32_t reserved;
 } mpm_stats;
 
 /* Fill *cfg with defaults (zeros except: block_size 4, material NH, E 1e6,
@@ -134,6 +136,25 @@ mpm_status mpm_config_default(mpm_config* cfg);
 mpm_status mpm_create(const mpm_config* cfg, int64_t n, const float* x, const float* v,
                       const float* C, const float* F, const float* phi_deg, int on_device,
                       void* stream, mpm_ctx** out);
+
+/* An ensemble: n_scenarios independent simulations in one context, every
+ * launch of a step covering all of them (the paper has no counterpart; it runs
+ * one simulation).  Scenario s has counts[s] >= 1 particles (host array); the
+ * particle arrays hold the scenarios one after another, in scenario order, and
+ * the particle ids follow that order.  Every scenario uses cfg as if it were
+ * alone: the same potential grid box, in its own frame (positions are never
+ * shifted), and the same constants; per-scenario friction angles go through
+ * phi_deg.  Inside the library scenario s's blocks sit s * (blocks of the box
+ * along x) further along x, so the scenarios share one hash table, active
+ * list and grid without touching each other, and boundary conditions are
+ * applied in each scenario's frame.  In MPM_DETERMINISTIC mode every scenario
+ * gives the same bits as a context holding that scenario alone.
+ * mpm_read_active returns the shifted block keys.  Not with MPM_DENSE_GRID.
+ * Errors: those of mpm_create; INVALID_ARG also when the shifted box leaves
+ * the Eq.-(key) range. */
+mpm_status mpm_create_ensemble(const mpm_config* cfg, int32_t n_scenarios, const int64_t* counts,
+                               const float* x, const float* v, const float* C, const float* F,
+                               const float* phi_deg, int on_device, void* stream, mpm_ctx** out);
 
 /* Active-set rebuild (Alg. 5-7): cell keys, hashed insert of every particle's
  * stencil blocks, regrowth on overflow, compaction to Phi in key order,

@@ -636,7 +636,8 @@ const char* mpm_last_error(const mpm_ctx* c) {
 }  // extern "C"
 
 static mpm_status create_impl(const mpm_config* cfg, int64_t n, const float* x, const float* v, const float* Cm,
-                              const float* F, const float* phi, int on_device, void* stream, mpm_ctx* c) {
+                              const float* F, const float* phi, int on_device, void* stream, mpm_ctx* c,
+                              int32_t n_scen, const int64_t* counts) {
     c->cfg = *cfg;
     c->cfg.terrain_height = nullptr;
     if (!c->cfg.max_probe) c->cfg.max_probe = 64;
@@ -660,6 +661,18 @@ static mpm_status create_impl(const mpm_config* cfg, int64_t n, const float* x, 
         P.blo[a] = (int)floordiv(cfg->domain_lo[a], c->B);
         P.nb[a] = (int)(floordiv(cfg->domain_hi[a], c->B) - P.blo[a] + 1);
         P.g[a] = (float)cfg->gravity[a];
+    }
+    P.n_scen = 1;
+    if (n_scen > 1) {
+        // scenario s's blocks follow scenario s - 1's along x
+        const int64_t nbx = (int64_t)P.nb[0] * n_scen;
+        if ((int64_t)P.blo[0] + nbx - 1 > ((int64_t)1 << 20) / c->B - 1)
+            return fail(c, MPM_ERR_INVALID_ARG, "the scenarios' boxes side by side leave the Eq. (key) range");
+        if (nbx * P.nb[1] * P.nb[2] >= ((int64_t)1 << 32))
+            return fail(c, MPM_ERR_INVALID_ARG, "the scenarios' boxes together hold 2^32 or more blocks");
+        P.n_scen = n_scen;
+        P.ens_pitch = P.nb[0];
+        P.nb[0] = (int)nbx;
     }
     c->n_dom_blocks = (int64_t)P.nb[0] * P.nb[1] * P.nb[2];
     P.h = (float)cfg->dx;
@@ -693,6 +706,15 @@ static mpm_status create_impl(const mpm_config* cfg, int64_t n, const float* x, 
         CK(dalloc(c, (void**)&c->pval[b], sizeof(uint32_t) * n));
     }
     if (counting_sort(c)) CK(dalloc(c, (void**)&c->prank, sizeof(uint32_t) * n));
+    if (n_scen > 1) {
+        std::vector<uint32_t> start(n_scen + 1, 0u);
+        for (int32_t k = 0; k < n_scen; ++k) start[k + 1] = start[k] + (uint32_t)counts[k];
+        CK(dalloc(c, (void**)&c->scen_start, sizeof(uint32_t) * (n_scen + 1)));
+        CK(cudaMemcpyAsync(c->scen_start, start.data(), sizeof(uint32_t) * (n_scen + 1), cudaMemcpyHostToDevice,
+                           c->st));
+        CK(cudaStreamSynchronize(c->st));   // the host vector goes out of scope
+        P.scen_start = c->scen_start;
+    }
     if (cfg->terrain_height) {
         const int64_t tn = (int64_t)cfg->terrain_nx * cfg->terrain_ny;
         CK(dalloc(c, (void**)&c->terrain, sizeof(float) * tn));
@@ -743,7 +765,34 @@ mpm_status mpm_create(const mpm_config* cfg, int64_t n, const float* x, const fl
     if (s != MPM_OK) return s;
     if (!x) return fail(nullptr, MPM_ERR_INVALID_ARG, "x is NULL");
     mpm_ctx* c = new mpm_ctx();
-    s = create_impl(cfg, n, x, v, C, F, phi_deg, on_device, stream, c);
+    s = create_impl(cfg, n, x, v, C, F, phi_deg, on_device, stream, c, 1, nullptr);
+    if (s != MPM_OK) {
+        g_create_error = c->last_error;
+        mpm_destroy(c);
+        return s;
+    }
+    *out = c;
+    return MPM_OK;
+}
+
+mpm_status mpm_create_ensemble(const mpm_config* cfg, int32_t n_scenarios, const int64_t* counts, const float* x,
+                               const float* v, const float* C, const float* F, const float* phi_deg, int on_device,
+                               void* stream, mpm_ctx** out) {
+    if (!out) return fail(nullptr, MPM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_scenarios < 1 || !counts) return fail(nullptr, MPM_ERR_INVALID_ARG, "need n_scenarios >= 1 and counts");
+    int64_t n = 0;
+    for (int32_t k = 0; k < n_scenarios; ++k) {
+        if (counts[k] < 1) return fail(nullptr, MPM_ERR_INVALID_ARG, "every scenario needs at least one particle");
+        n += counts[k];
+        if (n > (int64_t)INT32_MAX) return fail(nullptr, MPM_ERR_INVALID_ARG, "particle count out of range");
+    }
+    mpm_status s = validate(cfg, n);
+    if (s != MPM_OK) return s;
+    if (cfg->flags & MPM_DENSE_GRID) return fail(nullptr, MPM_ERR_INVALID_ARG, "ensembles run on the sparse grid only");
+    if (!x) return fail(nullptr, MPM_ERR_INVALID_ARG, "x is NULL");
+    mpm_ctx* c = new mpm_ctx();
+    s = create_impl(cfg, n, x, v, C, F, phi_deg, on_device, stream, c, n_scenarios, counts);
     if (s != MPM_OK) {
         g_create_error = c->last_error;
         mpm_destroy(c);
@@ -928,6 +977,7 @@ mpm_status mpm_get_stats(mpm_ctx* c, mpm_stats* o) {
     o->flags = (int32_t)c->cfg.flags;
     o->block_size = c->B;
     o->kernel_launches = c->launches;
+    o->n_scenarios = c->P.n_scen;
     return MPM_OK;
 }
 

@@ -91,7 +91,24 @@ struct Params {
     int wall_layers;
     int block_shift;             // log2(B)
     int max_probe;
+    // ensembles: scenario s occupies blocks [s * ens_pitch, (s + 1) * ens_pitch)
+    // along x of the block box (relative to blo); its particles keep their own
+    // frame and are the ids [scen_start[s], scen_start[s + 1]).
+    int n_scen;                  // 1 for a single simulation
+    int ens_pitch;               // blocks per scenario along x
+    const uint32_t* scen_start;  // device, n_scen + 1 entries (nullptr when n_scen == 1)
 };
+
+// Scenario of the particle with this id (binary search over scen_start).
+__device__ __forceinline__ int scenario_of(const Params& P, uint32_t id) {
+    int lo = 0, hi = P.n_scen;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(&P.scen_start[mid]) <= id) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
 
 struct HashView {
     unsigned long long* keys;
@@ -244,6 +261,9 @@ struct mpm_ctx {
 
     // terrain
     float* terrain = nullptr;
+
+    // ensemble
+    uint32_t* scen_start = nullptr;
 
     // status
     mpm::DevStatus* dstat = nullptr;

@@ -151,6 +151,8 @@ __global__ void __launch_bounds__(256) k_insert(const float* __restrict__ ps, in
         for (int j = 0; j < NJ; ++j)
             if (j / (R * R) < nbk[0] && (j / R) % R < nbk[1] && j % R < nbk[2]) need |= 1u << j;
     }
+    // An ensemble's scenario s has its blocks ens_pitch * s further along x.
+    if (P.n_scen > 1 && ok) b0[0] += scenario_of(P, __float_as_uint(ps[PID * stride + p])) * P.ens_pitch;
     // Lanes with the same base block form one group (particles are sorted, so
     // a warp usually holds one or two groups).  The group's union of needed
     // blocks is read from one ballot per block offset, and its members take

@@ -401,6 +401,7 @@ __global__ void __launch_bounds__(256) k_grid(int64_t cap, const DevStatus* st, 
         const int r = (int)(i >> S3), l = (int)(i & ((1 << S3) - 1));
         int bc[3];
         block_coords<DENSE>(P, bcoord, r, bc);
+        if (P.n_scen > 1) bc[0] -= ((bc[0] - P.blo[0]) / P.ens_pitch) * P.ens_pitch;   // the scenario's own frame
         const int n0 = bc[0] * B + l % B, n1 = bc[1] * B + (l / B) % B, n2 = bc[2] * B + l / (B * B);
         const float4 a = gmv[i];
         const float m = a.x;

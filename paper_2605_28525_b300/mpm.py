@@ -60,7 +60,7 @@ class Stats(C.Structure):
         ("n_particle_blocks", C.c_int64), ("n_dense_nodes", C.c_int64), ("hash_capacity", C.c_int64),
         ("block_capacity", C.c_int64), ("rebuild_rounds", C.c_int64), ("steps", C.c_int64),
         ("device_bytes", C.c_int64), ("kernel_launches", C.c_int64), ("flags", C.c_int32),
-        ("block_size", C.c_int32),
+        ("block_size", C.c_int32), ("n_scenarios", C.c_int32), ("reserved", C.c_int32),
     ]
 
     def as_dict(self):
@@ -72,7 +72,8 @@ _lib = None
 # every symbol the header declares (checked by tests/test_abi.py against include/mpm.h)
 EXPORTS = ("mpm_config_default", "mpm_create", "mpm_rebuild_active", "mpm_p2g", "mpm_grid_update", "mpm_g2p",
            "mpm_step", "mpm_read_particles", "mpm_write_particles", "mpm_read_active", "mpm_read_grid",
-           "mpm_get_stats", "mpm_status_string", "mpm_last_error", "mpm_destroy", "mpm_active_blocks_noalloc")
+           "mpm_get_stats", "mpm_status_string", "mpm_last_error", "mpm_destroy", "mpm_active_blocks_noalloc",
+           "mpm_create_ensemble")
 
 
 def lib():
@@ -87,6 +88,8 @@ def lib():
     vp, fp, i64 = C.c_void_p, C.POINTER(C.c_float), C.c_int64
     L.mpm_config_default.argtypes = [C.POINTER(Config)]
     L.mpm_create.argtypes = [C.POINTER(Config), i64, vp, vp, vp, vp, vp, C.c_int, vp, C.POINTER(vp)]
+    L.mpm_create_ensemble.argtypes = [C.POINTER(Config), C.c_int32, C.POINTER(C.c_int64), vp, vp, vp, vp, vp,
+                                      C.c_int, vp, C.POINTER(vp)]
     L.mpm_rebuild_active.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
     L.mpm_p2g.argtypes = [vp]
     L.mpm_grid_update.argtypes = [vp]
@@ -162,7 +165,8 @@ def _ptr(a):
 class Simulation:
     """One mpm_ctx.  Inputs: numpy float32 arrays (host) or torch CUDA tensors."""
 
-    def __init__(self, cfg: Config, x, v=None, C_=None, F=None, phi=None, stream=None, terrain=None):
+    def __init__(self, cfg: Config, x, v=None, C_=None, F=None, phi=None, stream=None, terrain=None,
+                 scenario_counts=None):
         L = lib()
         self._keep = []
         if terrain is not None:
@@ -187,7 +191,12 @@ class Simulation:
         if stream is not None:
             sptr = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
         h = C.c_void_p()
-        st = L.mpm_create(C.byref(cfg), n, *ptrs, 1 if device else 0, sptr, C.byref(h))
+        if scenario_counts is None:
+            st = L.mpm_create(C.byref(cfg), n, *ptrs, 1 if device else 0, sptr, C.byref(h))
+        else:
+            counts = np.ascontiguousarray(scenario_counts, dtype=np.int64)
+            st = L.mpm_create_ensemble(C.byref(cfg), len(counts), counts.ctypes.data_as(C.POINTER(C.c_int64)),
+                                       *ptrs, 1 if device else 0, sptr, C.byref(h))
         _check(st, None)
         self.h = h
 
@@ -199,8 +208,10 @@ class Simulation:
             x = torch.from_numpy(wl.x).cuda()
             v = torch.from_numpy(wl.v).cuda() if wl.v is not None else None
             phi = torch.from_numpy(wl.phi).cuda() if wl.phi is not None else None
-            return cls(cfg, x, v, None, None, phi, stream=stream, terrain=wl.terrain)
-        return cls(cfg, wl.x, wl.v, None, None, wl.phi, stream=stream, terrain=wl.terrain)
+            return cls(cfg, x, v, None, None, phi, stream=stream, terrain=wl.terrain,
+                       scenario_counts=wl.scenario_counts)
+        return cls(cfg, wl.x, wl.v, None, None, wl.phi, stream=stream, terrain=wl.terrain,
+                   scenario_counts=wl.scenario_counts)
 
     # ---- the step and its phases
     def rebuild_active(self):

@@ -18,6 +18,11 @@ Workloads (paper Sec. 2.2 examples; exact sizes in the design notes):
                              [25, 35] deg.
   * ``sliding_block``     -- elastic block on a Coulomb floor with tilted gravity
                              (the paper's sliding-box benchmark, Sec. 2.2.1).
+  * ``column_ensemble``   -- independent granular columns, one per scenario,
+                             each in its own 256x256x128 box at dx = 1/128:
+                             particle counts log-uniform in [1e4, 5e5], phi
+                             uniform in [20, 40] deg, height/width uniform in
+                             [0.5, 4].
 Particles are placed 2x2x2 per cell, each uniformly jittered inside its
 sub-cell, from a numpy PCG64 stream with the stated seed.  Positions are
 rounded to float32 once, here, so every consumer sees identical values.
@@ -59,6 +64,7 @@ class Workload:
     steps: int = 1
     block_size: int = 4
     wall_layers: int = 2
+    scenario_counts: Optional[np.ndarray] = None   # particles per scenario (ensembles), in order
 
     @property
     def n(self) -> int:
@@ -197,3 +203,42 @@ def random_state(n: int, lo_cell, hi_cell, dx: float, seed: int = 3, vscale: flo
     Cm = (cscale * rng.standard_normal((n, 3, 3))).astype(np.float32)
     F = (np.eye(3)[None] + fscale * rng.standard_normal((n, 3, 3))).astype(np.float32)
     return x, v, Cm, F
+
+
+def column_ensemble(n_scenarios: int = 64, seed: int = 4, n_min: int = 10_000, n_max: int = 500_000,
+                    steps: int = 1000) -> Workload:
+    """Independent Drucker-Prager columns, one per scenario, each centred in
+    its own 256x256x128-node box (dx = 1/128) on a Coulomb floor at z = 3 dx.
+    Per scenario: a particle count drawn log-uniform in [n_min, n_max], phi
+    uniform in [20, 40] deg and a height/width ratio uniform in [0.5, 4]; the
+    column is w x w x h cells at 8 particles per cell with w^2 h close to
+    count / 8.  Positions are in each scenario's own frame, concatenated in
+    scenario order; ``scenario_counts`` gives the split."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    dx = 1.0 / 128.0
+    xs, phis, counts = [], [], []
+    for s in range(n_scenarios):
+        n_target = math.exp(rng.uniform(math.log(n_min), math.log(n_max)))
+        phi = rng.uniform(20.0, 40.0)
+        aspect = rng.uniform(0.5, 4.0)
+        w = max(2, int(round((n_target / (8.0 * aspect)) ** (1.0 / 3.0))))
+        h = max(2, min(120, int(round(aspect * w))))
+        c0 = 128 - w // 2
+        x = jittered_cells((c0, c0, 3), (c0 + w, c0 + w, 3 + h), dx, seed * 1000 + s)
+        xs.append(x)
+        phis.append(np.full(x.shape[0], phi, np.float32))
+        counts.append(x.shape[0])
+    return Workload("column_ensemble_%d" % n_scenarios, (0, 0, 0), (256, 256, 128), dx, 2e-5, (0.0, 0.0, -9.81),
+                    DRUCKER_PRAGER, 1e7, 0.3, 2000.0, 30.0, 8.0, FLOOR_COULOMB, 3 * dx, 0.5,
+                    np.concatenate(xs), phi=np.concatenate(phis), steps=steps,
+                    scenario_counts=np.asarray(counts, np.int64))
+
+
+def ensemble_member(ens: Workload, s: int) -> Workload:
+    """Scenario s of an ensemble as a stand-alone workload (same box and
+    constants, its own particles)."""
+    c = np.concatenate([[0], np.cumsum(ens.scenario_counts)])
+    a, b = int(c[s]), int(c[s + 1])
+    return dataclasses.replace(ens, name="%s[%d]" % (ens.name, s), x=ens.x[a:b],
+                               v=None if ens.v is None else ens.v[a:b],
+                               phi=None if ens.phi is None else ens.phi[a:b], scenario_counts=None)
