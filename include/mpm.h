@@ -232,6 +232,31 @@ mpm_status mpm_active_blocks_noalloc(const float* x, int64_t n, const int32_t do
                                      const int32_t domain_hi[3], double dx, int32_t block_size,
                                      uint64_t* block_keys, int64_t cap, int64_t* n_active, void* stream);
 
+/* Launch shapes that change no result: how many P2G work CTAs run per SM,
+ * the G2P CTA size, and the register budget G2P was compiled for (the paper
+ * has no counterpart: these are this library's launch parameters). */
+typedef struct mpm_tuning {
+    int32_t p2g_ctas_per_sm;   /* 1..4 (default 4) */
+    int32_t g2p_threads;       /* 128 or 256 (default 256) */
+    int32_t g2p_min_blocks;    /* 2 (up to 128 registers a thread) or 3 (up to 80; default) */
+    int32_t reserved;
+    double p2g_ms, g2p_ms;     /* mpm_autotune: median device time of the chosen shapes */
+} mpm_tuning;
+
+/* Autotuner: runs one rebuild on the current state, then times P2G for each
+ * p2g_ctas_per_sm in 2..4 and G2P for each (g2p_threads, g2p_min_blocks) in
+ * {128, 256} x {2, 3}, `repeats` times each (CUDA events on the context's
+ * stream; the grid is cleared before every P2G), and keeps the shapes with
+ * the smallest median.  The particle state is not advanced: the step it
+ * timed is discarded.  Synchronises.  *out (nullable) receives the choice.
+ * Errors: those of mpm_rebuild_active; INVALID_ARG for repeats < 1. */
+mpm_status mpm_autotune(mpm_ctx* ctx, int32_t repeats, mpm_tuning* out);
+
+/* Read or set the launch shapes (set: INVALID_ARG outside the ranges above;
+ * the time fields are ignored). */
+mpm_status mpm_get_tuning(mpm_ctx* ctx, mpm_tuning* out);
+mpm_status mpm_set_tuning(mpm_ctx* ctx, const mpm_tuning* in);
+
 /* Static description of a status code; never NULL. */
 const char* mpm_status_string(mpm_status s);
 

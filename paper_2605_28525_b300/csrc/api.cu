@@ -955,6 +955,132 @@ mpm_status mpm_read_grid(mpm_ctx* c, float* m, float* mv, float* f, float* v, in
     return MPM_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+void fill_tuning(const mpm_ctx* c, mpm_tuning* o) {
+    std::memset(o, 0, sizeof(*o));
+    o->p2g_ctas_per_sm = c->tune.p2g_ctas_per_sm;
+    o->g2p_threads = c->tune.g2p_threads;
+    o->g2p_min_blocks = c->tune.g2p_min_blocks;
+}
+
+// Median of the device times of `repeats` runs of `run` (each bracketed by
+// events on the context's stream, after `prep`).
+template <class Prep, class Run>
+mpm_status time_median(mpm_ctx* c, int repeats, const Prep& prep, const Run& run, double* ms) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    std::vector<float> t;
+    mpm_status s = MPM_OK;
+    for (int k = 0; k < repeats && s == MPM_OK; ++k) {
+        cudaError_t e = prep();
+        if (e == cudaSuccess) e = cudaEventRecord(e0, c->st);
+        if (e == cudaSuccess) e = run();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, c->st);
+        if (e == cudaSuccess) e = sync_wait(c);
+        float x = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&x, e0, e1);
+        if (e != cudaSuccess) s = cuda_fail(c, e, "autotune timing");
+        t.push_back(x);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != MPM_OK) return s;
+    std::sort(t.begin(), t.end());
+    *ms = t[t.size() / 2];
+    return MPM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mpm_status mpm_autotune(mpm_ctx* c, int32_t repeats, mpm_tuning* out) {
+    if (!c || repeats < 1) return MPM_ERR_INVALID_ARG;
+    mpm_status s = do_rebuild(c);
+    if (s != MPM_OK) return s;
+    const int64_t nodes = c->n_active * c->B3;
+    // P2G accumulates into the grid and draws work units from a counter:
+    // both are reset before every run
+    const auto p2g_prep = [&]() -> cudaError_t {
+        cudaError_t e = cudaSuccess;
+        if (!c->det) {
+            e = cudaMemsetAsync(c->gmv, 0, sizeof(float4) * nodes, c->st);
+            if (e == cudaSuccess) e = cudaMemsetAsync(c->gf, 0, sizeof(float4) * nodes, c->st);
+        }
+        if (e == cudaSuccess) e = cudaMemsetAsync(&c->dstat->work, 0, sizeof(unsigned int), c->st);
+        return e;
+    };
+    const Tuning keep = c->tune;
+    double best_p2g = 1e30, best_g2p = 1e30;
+    Tuning best = keep;
+    for (int k = 2; k <= 4; ++k) {
+        c->tune.p2g_ctas_per_sm = k;
+        double ms = 0;
+        s = time_median(c, repeats, p2g_prep, [&]() { return launch_p2g(c); }, &ms);
+        if (s != MPM_OK) {
+            c->tune = keep;
+            return s;
+        }
+        if (ms < best_p2g) {
+            best_p2g = ms;
+            best.p2g_ctas_per_sm = k;
+        }
+    }
+    c->tune.p2g_ctas_per_sm = best.p2g_ctas_per_sm;
+    CK(p2g_prep());
+    CK(launch_p2g(c));
+    CK(launch_grid_update(c));
+    // G2P reads the current buffer and writes the other one: reruns repeat it
+    for (int threads = 128; threads <= 256; threads *= 2)
+        for (int mb = 2; mb <= 3; ++mb) {
+            c->tune.g2p_threads = threads;
+            c->tune.g2p_min_blocks = mb;
+            double ms = 0;
+            s = time_median(c, repeats, []() { return cudaSuccess; }, [&]() { return launch_g2p(c); }, &ms);
+            if (s != MPM_OK) {
+                c->tune = keep;
+                return s;
+            }
+            if (ms < best_g2p) {
+                best_g2p = ms;
+                best.g2p_threads = threads;
+                best.g2p_min_blocks = mb;
+            }
+        }
+    c->tune = best;
+    c->phase = 0;          // the timed step is discarded; the state is the one before it
+    ++c->cap_version;      // captured steps hold the old launch shapes
+    if (out) {
+        fill_tuning(c, out);
+        out->p2g_ms = best_p2g;
+        out->g2p_ms = best_g2p;
+    }
+    return MPM_OK;
+}
+
+mpm_status mpm_get_tuning(mpm_ctx* c, mpm_tuning* out) {
+    if (!c || !out) return MPM_ERR_INVALID_ARG;
+    fill_tuning(c, out);
+    return MPM_OK;
+}
+
+mpm_status mpm_set_tuning(mpm_ctx* c, const mpm_tuning* in) {
+    if (!c || !in) return MPM_ERR_INVALID_ARG;
+    if (in->p2g_ctas_per_sm < 1 || in->p2g_ctas_per_sm > 4 || (in->g2p_threads != 128 && in->g2p_threads != 256) ||
+        (in->g2p_min_blocks != 2 && in->g2p_min_blocks != 3))
+        return fail(c, MPM_ERR_INVALID_ARG, "tuning outside p2g_ctas_per_sm 1..4, g2p_threads 128/256, "
+                                            "g2p_min_blocks 2/3");
+    c->tune.p2g_ctas_per_sm = in->p2g_ctas_per_sm;
+    c->tune.g2p_threads = in->g2p_threads;
+    c->tune.g2p_min_blocks = in->g2p_min_blocks;
+    ++c->cap_version;
+    return MPM_OK;
+}
+
 mpm_status mpm_get_stats(mpm_ctx* c, mpm_stats* o) {
     if (!c || !o) return MPM_ERR_INVALID_ARG;
     std::memset(o, 0, sizeof(*o));

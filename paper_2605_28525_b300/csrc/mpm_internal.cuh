@@ -197,6 +197,13 @@ __device__ __forceinline__ void bspline_a(float d, int a, float& w, float& dw) {
 
 // ------------------------------------------------------------ host side
 
+// Launch shapes that change no result (mpm_autotune picks them).
+struct Tuning {
+    int p2g_ctas_per_sm = 4;     // persistent P2G grid: 148 x this many CTAs of 128 threads
+    int g2p_threads = 256;       // G2P CTA size (128 or 256)
+    int g2p_min_blocks = 3;      // G2P register budget: 3 (80 registers) or 2 (128) CTAs of 256 per SM
+};
+
 struct RadixScratch {
     uint32_t* counts = nullptr;   // [256][ntiles]
     uint32_t* totals = nullptr;   // [256]
@@ -270,6 +277,7 @@ struct mpm_ctx {
     mpm::DevStatus* hstat = nullptr;   // pinned
 
     mpm::RadixScratch rs;
+    mpm::Tuning tune;
 
     // staging for host <-> device particle copies
     float* stage = nullptr;

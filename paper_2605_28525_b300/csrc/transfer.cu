@@ -81,14 +81,6 @@ struct CellTileCfg {
 #ifndef MPM_P2G_MINB
 #define MPM_P2G_MINB 4
 #endif
-#ifndef MPM_G2P_MINB
-#define MPM_G2P_MINB 3     // 3 CTAs of 256 threads per SM: G2P is latency-bound, occupancy pays
-#endif
-#if MPM_G2P_MINB > 0
-#define MPM_G2P_BOUNDS __launch_bounds__(256, MPM_G2P_MINB)
-#else
-#define MPM_G2P_BOUNDS __launch_bounds__(256)
-#endif
 
 // The P2G inputs of one particle: x, v, C (scaled by h) and tau.
 struct P2GIn {
@@ -664,8 +656,10 @@ struct Neighbours {
 // neighbour table (L1-resident for the particles of one block).  The node
 // sums are factored over z: for each (a, b) the three z-nodes are first
 // reduced with w_z, dw_z and c w_z, then scattered into v_p, B_p and L_p.
-template <int B, bool DENSE, int MAT>
-__global__ void MPM_G2P_BOUNDS k_g2p(const float* __restrict__ ps, float* __restrict__ po, int64_t stride,
+// MINB: CTAs of 256 threads per SM the registers are sized for (2: up to 128
+// registers a thread, 3: up to 80); the autotuner picks one per context.
+template <int B, bool DENSE, int MAT, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_g2p(const float* __restrict__ ps, float* __restrict__ po, int64_t stride,
                                               const uint32_t* __restrict__ perm, const uint32_t* __restrict__ skey,
                                               int64_t n, const int* __restrict__ nbr, Params P,
                                               const float4* __restrict__ gv, DevStatus* st) {
@@ -826,7 +820,7 @@ __global__ void k_step_done(DevStatus* st) {
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-constexpr int PERSIST = 148 * MPM_P2G_MINB;   // CTAs of the block P2G (grid-stride over a device count)
+constexpr int NUM_SMS = 148;
 
 }  // namespace
 
@@ -841,7 +835,7 @@ cudaError_t launch_p2g(mpm_ctx* c) {
         return cudaGetLastError();
     }
 #define MPM_CELLS(D_, T_)                                                                                         \
-    k_p2g_cells<D_, T_><<<PERSIST, CellTileCfg::WARPS * 32, 0, c->ls>>>(ps, c->pstride, perm, c->bstart, c->bend, \
+    k_p2g_cells<D_, T_><<<NUM_SMS * c->tune.p2g_ctas_per_sm, CellTileCfg::WARPS * 32, 0, c->ls>>>(ps, c->pstride, perm, c->bstart, c->bend, \
                                                                        c->pblocks, c->ccount, c->dstat, c->P,   \
                                                                        c->nbr, c->gmv, c->gf, c->tbuf, c->dstat)
     if (c->dense) {
@@ -881,9 +875,18 @@ cudaError_t launch_g2p(mpm_ctx* c) {
     float* po = c->ps[1 - c->cur];
     const uint32_t* perm = c->pval[c->sorted_sel];
     const uint32_t* skey = c->pkey[c->sorted_sel];
-    const unsigned g = blocks_for(c->n, 256);
-#define MPM_G2P(B_, D_, M_)                                                                                       \
-    k_g2p<B_, D_, M_><<<g, 256, 0, c->ls>>>(ps, po, c->pstride, perm, skey, c->n, c->nbr, c->P, c->gv, c->dstat)
+    const int threads = c->tune.g2p_threads;
+    const unsigned g = blocks_for(c->n, threads);
+    const bool two = c->tune.g2p_min_blocks == 2;
+#define MPM_G2P(B_, D_, M_)                                                                                      \
+    do {                                                                                                         \
+        if (two)                                                                                                 \
+            k_g2p<B_, D_, M_, 2><<<g, threads, 0, c->ls>>>(ps, po, c->pstride, perm, skey, c->n, c->nbr, c->P,  \
+                                                           c->gv, c->dstat);                                     \
+        else                                                                                                     \
+            k_g2p<B_, D_, M_, 3><<<g, threads, 0, c->ls>>>(ps, po, c->pstride, perm, skey, c->n, c->nbr, c->P,  \
+                                                           c->gv, c->dstat);                                     \
+    } while (0)
     const int mat = c->P.material;
     if (c->B == 4) {
         if (c->dense) {

@@ -67,13 +67,21 @@ class Stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Tuning(C.Structure):
+    _fields_ = [("p2g_ctas_per_sm", C.c_int32), ("g2p_threads", C.c_int32), ("g2p_min_blocks", C.c_int32),
+                ("reserved", C.c_int32), ("p2g_ms", C.c_double), ("g2p_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
 _lib = None
 
 # every symbol the header declares (checked by tests/test_abi.py against include/mpm.h)
 EXPORTS = ("mpm_config_default", "mpm_create", "mpm_rebuild_active", "mpm_p2g", "mpm_grid_update", "mpm_g2p",
            "mpm_step", "mpm_read_particles", "mpm_write_particles", "mpm_read_active", "mpm_read_grid",
            "mpm_get_stats", "mpm_status_string", "mpm_last_error", "mpm_destroy", "mpm_active_blocks_noalloc",
-           "mpm_create_ensemble")
+           "mpm_create_ensemble", "mpm_autotune", "mpm_get_tuning", "mpm_set_tuning")
 
 
 def lib():
@@ -88,6 +96,9 @@ def lib():
     vp, fp, i64 = C.c_void_p, C.POINTER(C.c_float), C.c_int64
     L.mpm_config_default.argtypes = [C.POINTER(Config)]
     L.mpm_create.argtypes = [C.POINTER(Config), i64, vp, vp, vp, vp, vp, C.c_int, vp, C.POINTER(vp)]
+    L.mpm_autotune.argtypes = [vp, C.c_int32, C.POINTER(Tuning)]
+    L.mpm_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
+    L.mpm_set_tuning.argtypes = [vp, C.POINTER(Tuning)]
     L.mpm_create_ensemble.argtypes = [C.POINTER(Config), C.c_int32, C.POINTER(C.c_int64), vp, vp, vp, vp, vp,
                                       C.c_int, vp, C.POINTER(vp)]
     L.mpm_rebuild_active.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
@@ -270,6 +281,21 @@ class Simulation:
         fp = lambda a: a.ctypes.data_as(C.POINTER(C.c_float))
         _check(lib().mpm_read_grid(self.h, fp(m), fp(mv), fp(f), fp(v), max(nn, 1)), self.h)
         return {"m": m[:nn], "mv": mv[:nn], "f": f[:nn], "v": v[:nn]}
+
+    def autotune(self, repeats: int = 5) -> dict:
+        """mpm_autotune: time the launch shapes on the current state, keep the fastest."""
+        t = Tuning()
+        _check(lib().mpm_autotune(self.h, int(repeats), C.byref(t)), self.h)
+        return t.as_dict()
+
+    def tuning(self) -> dict:
+        t = Tuning()
+        _check(lib().mpm_get_tuning(self.h, C.byref(t)), self.h)
+        return t.as_dict()
+
+    def set_tuning(self, p2g_ctas_per_sm: int, g2p_threads: int, g2p_min_blocks: int):
+        t = Tuning(p2g_ctas_per_sm, g2p_threads, g2p_min_blocks, 0, 0.0, 0.0)
+        _check(lib().mpm_set_tuning(self.h, C.byref(t)), self.h)
 
     def stats(self):
         s = Stats()
