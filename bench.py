@@ -373,6 +373,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-flush", action="store_true")
+    ap.add_argument("--compaction", default="hash", choices=["hash", "scan"],
+                    help="active-set realisation: the hash (Sec. 4.3) or the scan (Sec. 4.2)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -395,7 +397,8 @@ def main():
         wl.n * STATE_BYTES_PER_PARTICLE / 1e6, L2_BYTES // 10 ** 6)) if flush is None else "flushed between steps"
     stream = torch.cuda.current_stream()
 
-    sim = mpm.Simulation.from_workload(wl, stream=stream, device_inputs=True)
+    cflags = mpm.SCAN_COMPACTION if args.compaction == "scan" else 0
+    sim = mpm.Simulation.from_workload(wl, flags=cflags, stream=stream, device_inputs=True)
     for _ in range(args.warmup):
         sim.step(1)
     tuning = sim.autotune(3)        # the library's own autotuner: launch shapes only, no result changes
@@ -463,7 +466,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(wl.describe(), l2=l2_note, step_launch="one mpm_step call of K steps (CUDA graphs)"
                            if flush is None else "mpm_step(1) per step",
-                           parallelism="replicas" if ws > 1 else "single GPU",
+                           parallelism="replicas" if ws > 1 else "single GPU", compaction=args.compaction,
                            tuning={k: tuning[k] for k in ("p2g_ctas_per_sm", "g2p_threads", "g2p_min_blocks")},
                            active_blocks=st["n_active_blocks"], particle_blocks=st["n_particle_blocks"]),
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",

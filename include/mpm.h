@@ -70,6 +70,11 @@ enum { MPM_FLOOR_NONE = 0, MPM_FLOOR_STICKY = 1, MPM_FLOOR_SLIP = 2, MPM_FLOOR_C
                                 synchronisation per step) instead of queueing the steps */
 #define MPM_NO_GRAPHS 8u     /* mpm_step queues its steps as plain kernel launches instead of
                                 replaying CUDA graphs (same kernels, same results) */
+#define MPM_SCAN_COMPACTION 16u /* the paper's scan realisation (Sec. 4.2, Alg. 2-4) in place of
+                                the hash (Sec. 4.3): a bit per block of the box, marked by every
+                                particle's stencil, and Phi = a scan of the marks; lookups are
+                                the scan itself, no table.  Same active set, same Phi, same
+                                results; memory grows with the box (n_blocks / 4 bytes) */
 
 /* Optional device allocator (e.g. a framework's caching allocator).  alloc
  * returns a device pointer of at least `bytes` bytes usable on `stream`, or
@@ -97,7 +102,7 @@ typedef struct mpm_config {
     double terrain_mu;                  /* Coulomb coefficient on nodes with z_n <= H */
     int32_t wall_layers;                /* sticky node layers at each box face (0: 2) */
     uint32_t flags;                     /* MPM_DETERMINISTIC | MPM_DENSE_GRID | MPM_SYNC_STEPS |
-                                           MPM_NO_GRAPHS */
+                                           MPM_NO_GRAPHS | MPM_SCAN_COMPACTION */
     int64_t hash_capacity;              /* initial H, power of two (0: automatic) */
     int64_t block_capacity;             /* initial active-block capacity (0: automatic) */
     int32_t max_probe;                  /* n_probe of Alg. 6 (0: 64) */

@@ -149,6 +149,8 @@ mpm_status validate(const mpm_config* cfg, int64_t n) {
     for (int a = 0; a < 3; ++a) nb *= floordiv(cfg->domain_hi[a], B) - floordiv(cfg->domain_lo[a], B) + 1;
     if (nb * B * B * B >= (int64_t)1 << 32)
         return fail(nullptr, MPM_ERR_INVALID_ARG, "box has 2^32 or more nodes (32-bit sort keys)");
+    if ((cfg->flags & MPM_SCAN_COMPACTION) && (cfg->flags & MPM_DENSE_GRID))
+        return fail(nullptr, MPM_ERR_INVALID_ARG, "MPM_SCAN_COMPACTION is a sparse-grid mode");
     if (cfg->material != MPM_NEOHOOKEAN && cfg->material != MPM_DRUCKER_PRAGER)
         return fail(nullptr, MPM_ERR_INVALID_ARG, "unknown material");
     if (!(cfg->E >= 0.0) || !(cfg->nu >= 0.0 && cfg->nu < 0.5) || !(cfg->rho > 0.0))
@@ -296,7 +298,8 @@ void rollback_g2p(mpm_ctx* c) {
 mpm_status do_rebuild(mpm_ctx* c) {
     // keep the table at most half full (Alg. 7 would recover too, at the cost
     // of a second insert)
-    if (!c->dense && 2 * c->n_active > c->H) CK(alloc_hash(c, 2 * c->H, std::max<int64_t>(c->block_cap, 2 * c->n_active)));
+    if (!c->dense && !c->scan && 2 * c->n_active > c->H)
+        CK(alloc_hash(c, 2 * c->H, std::max<int64_t>(c->block_cap, 2 * c->n_active)));
     c->ls = c->st;
     for (int round = 0;; ++round) {
         CK(clear_retry_flags(c));
@@ -315,7 +318,7 @@ mpm_status do_rebuild(mpm_ctx* c) {
         }
         c->g2p_swapped = false;
         if (s.out_of_domain) return fail(c, MPM_ERR_OUT_OF_DOMAIN, "a particle stencil left the potential grid box");
-        if (c->dense || !s.overflow) break;
+        if (c->dense || c->scan || !s.overflow) break;   // a scan-mode count never exceeds the box
         // Alg. 7: enlarge and insert again
         if (round >= c->cfg.max_rebuilds)
             return fail(c, MPM_ERR_HASH_OVERFLOW, "hash table still overflows after max_rebuilds regrowth rounds");
@@ -441,7 +444,7 @@ mpm_status capture_step(mpm_ctx* c, int parity) {
 mpm_status prepare_batch(mpm_ctx* c) {
     const int64_t est = std::max(c->est_active, c->n_active);
     const int64_t want = c->dense ? c->n_dom_blocks : est + est / 2 + 64;
-    if (!c->dense) {
+    if (!c->dense && !c->scan) {
         const int64_t H = std::max<int64_t>({next_pow2(2 * want), c->H, c->min_H});
         if (c->block_cap < want || c->H < H) CK(alloc_hash(c, H, std::max(c->block_cap, want)));
     }
@@ -647,6 +650,7 @@ static mpm_status create_impl(const mpm_config* cfg, int64_t n, const float* x, 
     c->ls = c->st;
     CK(cudaGetDevice(&c->device));
     c->dense = (cfg->flags & MPM_DENSE_GRID) != 0;
+    c->scan = (cfg->flags & MPM_SCAN_COMPACTION) != 0;
     c->det = (cfg->flags & MPM_DETERMINISTIC) != 0;
     c->B = cfg->block_size;
     c->B3 = c->B * c->B * c->B;
@@ -735,10 +739,17 @@ static mpm_status create_impl(const mpm_config* cfg, int64_t n, const float* x, 
             CK(dalloc(c, (void**)&c->bmask, sizeof(uint32_t) * words));
             CK(dalloc(c, (void**)&c->bpre, sizeof(int) * (words + 1)));
             CK(dalloc(c, (void**)&c->btsum, sizeof(int) * (words / 2048 + 2)));
+        } else if (c->scan) {
+            return fail(c, MPM_ERR_INVALID_ARG, "MPM_SCAN_COMPACTION: the box's block mask would exceed 64 MiB");
         }
-        int64_t cap = cfg->block_capacity ? cfg->block_capacity : std::max<int64_t>(1024, n / 32);
-        int64_t H = cfg->hash_capacity ? cfg->hash_capacity : next_pow2(2 * cap);
-        CK(alloc_hash(c, H, cap));
+        if (c->scan) {   // no table: any block of the box may be marked
+            c->block_cap = c->n_dom_blocks;
+            CK(radix_reserve(c, n));
+        } else {
+            int64_t cap = cfg->block_capacity ? cfg->block_capacity : std::max<int64_t>(1024, n / 32);
+            int64_t H = cfg->hash_capacity ? cfg->hash_capacity : next_pow2(2 * cap);
+            CK(alloc_hash(c, H, cap));
+        }
     }
     mpm_status s = load_arrays(c, c->ps[0], x, v, Cm, F, on_device, true);
     if (s != MPM_OK) return s;

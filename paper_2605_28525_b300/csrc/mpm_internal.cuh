@@ -110,10 +110,14 @@ __device__ __forceinline__ int scenario_of(const Params& P, uint32_t id) {
     return lo;
 }
 
+// Block lookup: the hash table (Sec. 4.3), or in scan mode the block bit
+// mask and its word-count scan (Sec. 4.2), where Phi = set bits below.
 struct HashView {
     unsigned long long* keys;
     int* vals;
     uint64_t mask;               // H - 1
+    const uint32_t* bits = nullptr;   // scan mode: bit per block of the box
+    const int* pre = nullptr;         // scan mode: exclusive scan of the words' bit counts
 };
 
 // ------------------------------------------------------------------ keys
@@ -158,6 +162,25 @@ __device__ __forceinline__ int hash_find(const HashView& hv, uint64_t key, int m
         s = (s + 1) & hv.mask;
     }
     return -1;
+}
+
+// Scan mode: Phi of the block with relative key rel, -1 if it is not marked.
+__device__ __forceinline__ int mask_rank(const HashView& hv, uint32_t rel) {
+    const uint32_t w = rel >> 5, b = 1u << (rel & 31u);
+    const uint32_t word = __ldg(&hv.bits[w]);
+    if (!(word & b)) return -1;
+    return __ldg(&hv.pre[w]) + __popc(word & (b - 1u));
+}
+
+// Phi of block (bi, bj, bk): the table or the scan; -1 if absent.
+__device__ __forceinline__ int lookup_block(const Params& P, const HashView& hv, int bi, int bj, int bk) {
+    if (hv.bits) {
+        if (bi < P.blo[0] || bj < P.blo[1] || bk < P.blo[2] || bi >= P.blo[0] + P.nb[0] ||
+            bj >= P.blo[1] + P.nb[1] || bk >= P.blo[2] + P.nb[2])
+            return -1;
+        return mask_rank(hv, rel_key(P, bi, bj, bk));
+    }
+    return hash_find(hv, pack_key(bi, bj, bk), P.max_probe);
 }
 
 // ---------------------------------------------------- quadratic B-spline
@@ -235,6 +258,7 @@ struct mpm_ctx {
     int* bpre = nullptr;         // exclusive scan of the words' bit counts (+ total): Phi = rank
     int* btsum = nullptr;        // scan tile totals
     int64_t bwords = 0;          // words of bmask (0: the block keys are radix-sorted instead)
+    bool scan = false;           // MPM_SCAN_COMPACTION: no hash table, Phi and lookups from bmask
     int64_t block_cap = 0;
     int64_t live_cap = 0;        // active blocks every per-step array can hold (<= block_cap)
     int64_t n_dom_blocks = 0;
@@ -322,6 +346,7 @@ void set_noctx_error(const std::string& why);
 
 // ---- rebuild (rebuild.cu)
 cudaError_t launch_insert(mpm_ctx* c, int64_t ins_cap);
+HashView hash_view(const mpm_ctx* c);
 cudaError_t launch_dense_codes(mpm_ctx* c);
 cudaError_t launch_assign(mpm_ctx* c);
 cudaError_t launch_particle_keys(mpm_ctx* c);

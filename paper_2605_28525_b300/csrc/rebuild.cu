@@ -123,7 +123,10 @@ __device__ __forceinline__ bool particle_base(const float* __restrict__ ps, int6
     return ok;
 }
 
-template <int B>
+// SCAN: the scan realisation (Sec. 4.2, Alg. 2): each needed block's bit is
+// set in the mask and the particle's code holds its base block's relative key;
+// no table.  Otherwise Alg. 6 as above, and the code holds the table slot.
+template <int B, bool SCAN>
 __global__ void __launch_bounds__(256) k_insert(const float* __restrict__ ps, int64_t stride, int64_t n,
                                                 Params P, HashView hv, uint32_t* __restrict__ akey,
                                                 uint32_t* __restrict__ aslot, int64_t cap,
@@ -175,8 +178,15 @@ __global__ void __launch_bounds__(256) k_insert(const float* __restrict__ ps, in
             for (int q = 0; q < t; ++q) m &= m - 1u;
             const int j = __ffs(m) - 1;
             const int bi = b0[0] + j / (R * R), bj = b0[1] + (j / R) % R, bk = b0[2] + j % R;
-            const int slot = hash_insert(hv, pack_key(bi, bj, bk), rel_key(P, bi, bj, bk), P.max_probe, akey, aslot,
-                                         cap, bmask, st);
+            int slot;
+            if (SCAN) {
+                const uint32_t rk = rel_key(P, bi, bj, bk), bit = 1u << (rk & 31u);
+                if (!(*((volatile uint32_t*)&bmask[rk >> 5]) & bit)) atomicOr(&bmask[rk >> 5], bit);
+                slot = (int)rk;
+            } else {
+                slot = hash_insert(hv, pack_key(bi, bj, bk), rel_key(P, bi, bj, bk), P.max_probe, akey, aslot, cap,
+                                   bmask, st);
+            }
             if (j == 0) myslot = slot;   // bit 0 (the base block) is taken by rank 0 = the leader
         }
     }
@@ -255,6 +265,46 @@ __global__ void k_assign_bits(const uint32_t* __restrict__ akey, const uint32_t*
     if (bins) bins[node] = 0;
 }
 
+// Scan mode: block coordinates per Phi from the marked bits (thread per mask
+// word), and the live grid nodes and counting-sort bins zeroed.
+__global__ void k_assign_scan(const uint32_t* __restrict__ bmask, const int* __restrict__ bpre, int64_t words,
+                              int64_t cap, const DevStatus* st, Params P, int4* __restrict__ bcoord,
+                              float4* __restrict__ gmv, float4* __restrict__ gf, int* __restrict__ bins, int B3,
+                              int zero_grid) {
+    if (cta_aborted(st)) return;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t w = t0; w < words; w += stride) {
+        uint32_t m = bmask[w];
+        int64_t r = bpre[w];
+        while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1u;
+            int bi, bj, bk;
+            rel_decode(P, (uint32_t)(w * 32 + b), bi, bj, bk);
+            if (r < cap) bcoord[r] = make_int4(bi, bj, bk, 0);
+            ++r;
+        }
+    }
+    const int64_t nn = live_blocks(st, cap) * B3;
+    for (int64_t i = t0; i < nn; i += stride) {
+        if (zero_grid) {
+            gmv[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            gf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        if (bins) bins[i] = 0;
+    }
+}
+
+// Scan mode: the block count is the scan's total; beyond the capacity the
+// step stops (overflow bit 1, as for the table's list).
+__global__ void k_scan_count(const int* __restrict__ bpre, int64_t words, int64_t cap, DevStatus* st) {
+    if (st->go == 0u) return;
+    const unsigned tot = (unsigned)bpre[words];
+    st->n_active = tot;
+    if ((int64_t)tot > cap) raise_flag(st, &st->overflow, 2u);
+}
+
 // Phi of the blocks b + {0..R-1}^3 of every active block (runs after
 // k_assign, once every table value holds its rank).
 template <int B>
@@ -269,7 +319,7 @@ __global__ void k_neighbours(const int4* __restrict__ bcoord, int64_t cap, const
     const int64_t r = t / NNB;
     const int e = (int)(t % NNB);
     const int4 b = bcoord[r];
-    nbr[t] = hash_find(hv, pack_key(b.x + e / (R * R), b.y + (e / R) % R, b.z + e % R), P.max_probe);
+    nbr[t] = lookup_block(P, hv, b.x + e / (R * R), b.y + (e / R) % R, b.z + e % R);
 }
 
 __global__ void k_zero_grid(float4* __restrict__ gmv, float4* __restrict__ gf, int64_t nn, const DevStatus* st) {
@@ -284,7 +334,7 @@ __global__ void k_zero_grid(float4* __restrict__ gmv, float4* __restrict__ gf, i
 // written at the particle's id so that the stable sort breaks ties by id.
 template <bool DENSE>
 __global__ void k_particle_keys(const float* __restrict__ ps, int64_t stride, int64_t n,
-                                const uint32_t* __restrict__ pcode, const int* __restrict__ hvals, int B3,
+                                const uint32_t* __restrict__ pcode, HashView hv, int B3,
                                 int by_id, uint32_t* __restrict__ key, uint32_t* __restrict__ val,
                                 DevStatus* st) {
     if (cta_aborted(st)) return;
@@ -295,7 +345,8 @@ __global__ void k_particle_keys(const float* __restrict__ ps, int64_t stride, in
     if (DENSE) {
         k = code;
     } else {
-        const int r = code == 0xffffffffu ? -1 : hvals[code / (uint32_t)B3];
+        const uint32_t q = code / (uint32_t)B3;   // table slot, or the block's relative key in scan mode
+        const int r = code == 0xffffffffu ? -1 : (hv.bits ? mask_rank(hv, q) : hv.vals[q]);
         if (r < 0) {
             raise_flag(st, &st->map_miss, 1u);
             k = 0xffffffffu;   // sorts last; k_ranges ignores it
@@ -398,7 +449,7 @@ __global__ void __launch_bounds__(128) k_interleave(const uint32_t* __restrict__
 // bin: lanes of a warp with the same key take consecutive ranks from one
 // atomic add by their leader.
 __global__ void __launch_bounds__(256) k_particle_bins(int64_t n, const uint32_t* __restrict__ pcode,
-                                                       const int* __restrict__ hvals, int B3, int* __restrict__ bins,
+                                                       HashView hv, int B3, int* __restrict__ bins,
                                                        uint32_t* __restrict__ key, uint32_t* __restrict__ prank,
                                                        DevStatus* st) {
     if (cta_aborted(st)) return;
@@ -408,7 +459,8 @@ __global__ void __launch_bounds__(256) k_particle_bins(int64_t n, const uint32_t
     uint32_t k = 0xffffffffu;
     if (p < n) {
         const uint32_t code = pcode[p];
-        const int r = code == 0xffffffffu ? -1 : hvals[code / (uint32_t)B3];
+        const uint32_t q = code / (uint32_t)B3;
+        const int r = code == 0xffffffffu ? -1 : (hv.bits ? mask_rank(hv, q) : hv.vals[q]);
         if (r < 0) raise_flag(st, &st->map_miss, 1u);
         else k = (uint32_t)r * (uint32_t)B3 + code % (uint32_t)B3;
     }
@@ -589,18 +641,40 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 // (c->n, c->H, c->live_cap); live counts come from the status words, so the
 // same launch sequence serves any step and can be captured in a graph.
 
+HashView hash_view(const mpm_ctx* c) {
+    HashView hv{c->hkeys, c->hvals, (uint64_t)(c->H ? c->H - 1 : 0)};
+    if (c->scan) {
+        hv.bits = c->bmask;
+        hv.pre = c->bpre;
+    }
+    return hv;
+}
+
 cudaError_t launch_insert(mpm_ctx* c, int64_t ins_cap) {
-    HashView hv{c->hkeys, c->hvals, (uint64_t)(c->H - 1)};
-    const unsigned gc = (unsigned)std::min<int64_t>(blocks_for(c->H, 256), 148 * 16);
+    const HashView hv = hash_view(c);
+    const unsigned gc = (unsigned)std::min<int64_t>(blocks_for(std::max<int64_t>(c->H, c->bwords), 256), 148 * 16);
     k_hash_clear<<<gc, 256, 0, c->ls>>>(c->hkeys, c->hvals, c->H, c->bmask, c->bwords, c->dstat);
     c->launches += 2;
     const float* ps = c->ps[c->cur];
-    if (c->B == 4)
-        k_insert<4><<<blocks_for(c->n, 256), 256, 0, c->ls>>>(ps, c->pstride, c->n, c->P, hv, c->akey[0], c->aslot[0],
-                                                              ins_cap, c->bmask, c->pcode, c->dstat);
-    else
-        k_insert<1><<<blocks_for(c->n, 256), 256, 0, c->ls>>>(ps, c->pstride, c->n, c->P, hv, c->akey[0], c->aslot[0],
-                                                              ins_cap, c->bmask, c->pcode, c->dstat);
+#define MPM_INS(B_, S_)                                                                                           \
+    k_insert<B_, S_><<<blocks_for(c->n, 256), 256, 0, c->ls>>>(ps, c->pstride, c->n, c->P, hv, c->akey[0],       \
+                                                               c->aslot[0], ins_cap, c->bmask, c->pcode, c->dstat)
+    if (c->B == 4) {
+        if (c->scan) MPM_INS(4, true);
+        else MPM_INS(4, false);
+    } else {
+        if (c->scan) MPM_INS(1, true);
+        else MPM_INS(1, false);
+    }
+#undef MPM_INS
+    if (c->scan) {   // Alg. 3: the scan of the marks gives the block count before the host reads it
+        const int ntiles = (int)((c->bwords + SC_TILE - 1) / SC_TILE);
+        k_bits_scan_tiles<<<ntiles, SC_THREADS, 0, c->ls>>>(c->bmask, c->bwords, c->dstat, c->bpre, c->btsum);
+        k_scan_sums<<<1, 1024, 0, c->ls>>>(c->btsum, ntiles, c->dstat);
+        k_scan_add_n<<<blocks_for(c->bwords + 1, 256), 256, 0, c->ls>>>(c->bpre, c->bwords, c->dstat, c->btsum, ntiles);
+        k_scan_count<<<1, 1, 0, c->ls>>>(c->bpre, c->bwords, ins_cap, c->dstat);
+        c->launches += 4;
+    }
     return cudaGetLastError();
 }
 
@@ -626,7 +700,13 @@ cudaError_t launch_assign(mpm_ctx* c) {
         return cudaGetLastError();
     }
     int* bins = counting_sort(c) ? c->bins : nullptr;
-    if (c->bmask) {
+    if (c->scan) {   // Alg. 4: block coordinates per Phi from the scanned marks
+        const unsigned g = (unsigned)std::min<int64_t>(blocks_for(std::max<int64_t>(c->bwords, cap * c->B3), 256),
+                                                       148 * 16);
+        k_assign_scan<<<g, 256, 0, c->ls>>>(c->bmask, c->bpre, c->bwords, cap, c->dstat, c->P, c->bcoord, c->gmv, c->gf,
+                                            bins, c->B3, zero);
+        ++c->launches;
+    } else if (c->bmask) {
         const int ntiles = (int)((c->bwords + SC_TILE - 1) / SC_TILE);
         k_bits_scan_tiles<<<ntiles, SC_THREADS, 0, c->ls>>>(c->bmask, c->bwords, c->dstat, c->bpre, c->btsum);
         k_scan_sums<<<1, 1024, 0, c->ls>>>(c->btsum, ntiles, c->dstat);
@@ -643,7 +723,7 @@ cudaError_t launch_assign(mpm_ctx* c) {
                                                                   zero);
         ++c->launches;
     }
-    HashView hv{c->hkeys, c->hvals, (uint64_t)(c->H - 1)};
+    const HashView hv = hash_view(c);
     const int nnb = c->B == 4 ? 8 : 27;
     if (c->B == 4)
         k_neighbours<4><<<blocks_for(cap * nnb, 256), 256, 0, c->ls>>>(c->bcoord, cap, c->dstat, c->P, hv, c->nbr);
@@ -661,7 +741,7 @@ cudaError_t launch_particle_keys(mpm_ctx* c) {
     const int64_t nkeys = cap * c->B3;
     if (counting_sort(c)) {
         // one pass: key + rank in bin; scan of the bins; scatter
-        k_particle_bins<<<blocks_for(c->n, 256), 256, 0, c->ls>>>(c->n, c->pcode, c->hvals, c->B3, c->bins, c->pkey[0],
+        k_particle_bins<<<blocks_for(c->n, 256), 256, 0, c->ls>>>(c->n, c->pcode, hash_view(c), c->B3, c->bins, c->pkey[0],
                                                                   c->prank, c->dstat);
         const int ntiles = (int)((nkeys + SC_TILE - 1) / SC_TILE);
         k_scan_tiles<<<ntiles, SC_THREADS, 0, c->ls>>>(c->bins, cap, c->B3, c->dstat, c->cs, c->tsum);
@@ -675,10 +755,10 @@ cudaError_t launch_particle_keys(mpm_ctx* c) {
     }
     const int by_id = c->det ? 1 : 0;
     if (c->dense)
-        k_particle_keys<true><<<blocks_for(c->n, 256), 256, 0, c->ls>>>(ps, c->pstride, c->n, c->pcode, nullptr, c->B3,
+        k_particle_keys<true><<<blocks_for(c->n, 256), 256, 0, c->ls>>>(ps, c->pstride, c->n, c->pcode, hash_view(c), c->B3,
                                                                        by_id, c->pkey[0], c->pval[0], c->dstat);
     else
-        k_particle_keys<false><<<blocks_for(c->n, 256), 256, 0, c->ls>>>(ps, c->pstride, c->n, c->pcode, c->hvals, c->B3,
+        k_particle_keys<false><<<blocks_for(c->n, 256), 256, 0, c->ls>>>(ps, c->pstride, c->n, c->pcode, hash_view(c), c->B3,
                                                                         by_id, c->pkey[0], c->pval[0], c->dstat);
     ++c->launches;
     cudaError_t e = cudaGetLastError();

@@ -54,7 +54,7 @@ __device__ __forceinline__ int block_rank(const Params& P, const HashView& hv, i
             return -1;
         return (int)rel_key(P, bi, bj, bk);
     }
-    return hash_find(hv, pack_key(bi, bj, bk), P.max_probe);
+    return lookup_block(P, hv, bi, bj, bk);
 }
 
 // ------------------------------------------------------- P2G: cell lanes
@@ -827,7 +827,7 @@ constexpr int NUM_SMS = 148;
 cudaError_t launch_p2g(mpm_ctx* c) {
     const float* ps = c->ps[c->cur];
     const uint32_t* perm = c->pval[c->sorted_sel];
-    HashView hv{c->hkeys, c->hvals, (uint64_t)(c->H ? c->H - 1 : 0)};
+    const HashView hv = hash_view(c);
     if (c->B == 1) {
         k_p2g_atomic<<<blocks_for(c->n, 256), 256, 0, c->ls>>>(ps, c->pstride, perm, c->pkey[c->sorted_sel], c->n,
                                                               c->nbr, c->P, c->gmv, c->gf, c->dstat);

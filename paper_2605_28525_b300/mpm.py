@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(_HERE, "libmpm_b300.so")
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_HASH_OVERFLOW, ERR_OUT_OF_DOMAIN, ERR_NUMERIC, ERR_CUDA, ERR_STATE = range(8)
 NEOHOOKEAN, DRUCKER_PRAGER = 0, 1
 FLOOR_NONE, FLOOR_STICKY, FLOOR_SLIP, FLOOR_COULOMB = 0, 1, 2, 3
-DETERMINISTIC, DENSE_GRID, SYNC_STEPS, NO_GRAPHS = 1, 2, 4, 8
+DETERMINISTIC, DENSE_GRID, SYNC_STEPS, NO_GRAPHS, SCAN_COMPACTION = 1, 2, 4, 8, 16
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
