@@ -241,7 +241,7 @@ mpm_status mpm_active_blocks_noalloc(const float* x, int64_t n, const int32_t do
  * the G2P CTA size, and the register budget G2P was compiled for (the paper
  * has no counterpart: these are this library's launch parameters). */
 typedef struct mpm_tuning {
-    int32_t p2g_ctas_per_sm;   /* 1..4 (default 4) */
+    int32_t p2g_ctas_per_sm;   /* 1..8 (default: the most that fit on an SM) */
     int32_t g2p_threads;       /* 128 or 256 (default 256) */
     int32_t g2p_min_blocks;    /* 2 (up to 128 registers a thread) or 3 (up to 80; default) */
     int32_t reserved;
@@ -249,7 +249,8 @@ typedef struct mpm_tuning {
 } mpm_tuning;
 
 /* Autotuner: runs one rebuild on the current state, then times P2G for each
- * p2g_ctas_per_sm in 2..4 and G2P for each (g2p_threads, g2p_min_blocks) in
+ * even p2g_ctas_per_sm up to the most that fit on an SM, and G2P for each
+ * (g2p_threads, g2p_min_blocks) in
  * {128, 256} x {2, 3}, `repeats` times each (CUDA events on the context's
  * stream; the grid is cleared before every P2G), and keeps the shapes with
  * the smallest median.  The particle state is not advanced: the step it

@@ -1028,7 +1028,7 @@ mpm_status mpm_autotune(mpm_ctx* c, int32_t repeats, mpm_tuning* out) {
     const Tuning keep = c->tune;
     double best_p2g = 1e30, best_g2p = 1e30;
     Tuning best = keep;
-    for (int k = 2; k <= 4; ++k) {
+    for (int k = 2; k <= MPM_P2G_MAX_CTAS; k += 2) {
         c->tune.p2g_ctas_per_sm = k;
         double ms = 0;
         s = time_median(c, repeats, p2g_prep, [&]() { return launch_p2g(c); }, &ms);
@@ -1081,9 +1081,9 @@ mpm_status mpm_get_tuning(mpm_ctx* c, mpm_tuning* out) {
 
 mpm_status mpm_set_tuning(mpm_ctx* c, const mpm_tuning* in) {
     if (!c || !in) return MPM_ERR_INVALID_ARG;
-    if (in->p2g_ctas_per_sm < 1 || in->p2g_ctas_per_sm > 4 || (in->g2p_threads != 128 && in->g2p_threads != 256) ||
+    if (in->p2g_ctas_per_sm < 1 || in->p2g_ctas_per_sm > 8 || (in->g2p_threads != 128 && in->g2p_threads != 256) ||
         (in->g2p_min_blocks != 2 && in->g2p_min_blocks != 3))
-        return fail(c, MPM_ERR_INVALID_ARG, "tuning outside p2g_ctas_per_sm 1..4, g2p_threads 128/256, "
+        return fail(c, MPM_ERR_INVALID_ARG, "tuning outside p2g_ctas_per_sm 1..8, g2p_threads 128/256, "
                                             "g2p_min_blocks 2/3");
     c->tune.p2g_ctas_per_sm = in->p2g_ctas_per_sm;
     c->tune.g2p_threads = in->g2p_threads;

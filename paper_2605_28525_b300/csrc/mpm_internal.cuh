@@ -220,9 +220,14 @@ __device__ __forceinline__ void bspline_a(float d, int a, float& w, float& dw) {
 
 // ------------------------------------------------------------ host side
 
+// CTAs of the P2G kernel that fit on one SM (registers and shared memory).
+#ifndef MPM_P2G_MAX_CTAS
+#define MPM_P2G_MAX_CTAS 4
+#endif
+
 // Launch shapes that change no result (mpm_autotune picks them).
 struct Tuning {
-    int p2g_ctas_per_sm = 4;     // persistent P2G grid: 148 x this many CTAs of 128 threads
+    int p2g_ctas_per_sm = MPM_P2G_MAX_CTAS;   // persistent P2G grid: 148 x this many CTAs of 128 threads
     int g2p_threads = 256;       // G2P CTA size (128 or 256)
     int g2p_min_blocks = 3;      // G2P register budget: 3 (80 registers) or 2 (128) CTAs of 256 per SM
 };

@@ -142,6 +142,10 @@ __device__ __forceinline__ void p2g_accumulate(const Params& P, const P2GIn& in,
     }
 }
 
+#ifndef MPM_P2G_PCACHE
+#define MPM_P2G_PCACHE 8   // rounds whose particle indices a lane loads once per half block
+#endif
+
 template <bool DENSE, bool DET>
 __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, MPM_P2G_MINB) k_p2g_cells(
     const float* __restrict__ ps, int64_t stride, const uint32_t* __restrict__ perm,
@@ -179,6 +183,22 @@ __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, MPM_P2G_MINB) k_p2g_c
         for (int h = h0; h < h1; ++h) {
             const int cnt = h ? cnt1 : cnt0;
             const int cx = lane & 3, cy = (lane >> 2) & 3, cz = 2 * h + (lane >> 4) - zoff;
+#if MPM_P2G_PCACHE
+            // storage indices of this lane's first rounds, loaded once for the
+            // three x-offset passes (one dependent load less per round)
+            uint32_t pc[MPM_P2G_PCACHE];
+            {
+                int off = 0;
+#pragma unroll
+                for (int k = 0; k < MPM_P2G_PCACHE; ++k) {
+                    const unsigned M0 = __ballot_sync(FULL, cnt0 > k), M1 = __ballot_sync(FULL, cnt1 > k);
+                    const int idx = h ? __popc(M0) + __popc(M1 & lt) : __popc(M0 & lt);
+                    const int nrun = __popc(M0) + __popc(M1);
+                    pc[k] = (cnt > k && off + nrun <= kcap) ? perm[s + off + idx] : 0u;
+                    off += nrun;
+                }
+            }
+#endif
 #pragma unroll 1
             for (int a = 0; a < 3; ++a) {
                 float acc[3][3][7];
@@ -199,9 +219,20 @@ __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, MPM_P2G_MINB) k_p2g_c
                         break;
                     }
                     if (cnt > k) {
-                        const int idx = h ? __popc(M0) + __popc(M1 & lt) : __popc(M0 & lt);
+                        uint32_t p;
+#if MPM_P2G_PCACHE
+                        if (k < MPM_P2G_PCACHE) {
+                            p = pc[0];
+#pragma unroll
+                            for (int q = 1; q < MPM_P2G_PCACHE; ++q) p = (k == q) ? pc[q] : p;
+                        } else
+#endif
+                        {
+                            const int idx = h ? __popc(M0) + __popc(M1 & lt) : __popc(M0 & lt);
+                            p = perm[s + off + idx];
+                        }
                         P2GIn in;
-                        in.load(ps, stride, perm[s + off + idx], P.h);
+                        in.load(ps, stride, p, P.h);
                         p2g_accumulate(P, in, a, acc);
                     }
                     off += __popc(M0) + __popc(M1);

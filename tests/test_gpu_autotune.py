@@ -49,7 +49,7 @@ def test_every_shape_gives_the_same_bits(oracle_mod, shape):
 def test_set_tuning_rejects_out_of_range(oracle_mod):
     wl = W.elastic_cube(steps=1)
     a = mpm.Simulation.from_workload(wl)
-    for bad in [(0, 256, 3), (5, 256, 3), (4, 512, 3), (4, 256, 4)]:
+    for bad in [(0, 256, 3), (9, 256, 3), (4, 512, 3), (4, 256, 4)]:
         with pytest.raises(mpm.MpmError) as e:
             a.set_tuning(*bad)
         assert e.value.status == mpm.ERR_INVALID_ARG
