@@ -80,7 +80,12 @@ __device__ int hash_insert(const HashView& hv, uint64_t key, uint32_t rkey, int 
             unsigned long long old = atomicCAS(&hv.keys[s], EMPTY_KEY, (unsigned long long)key);
             if (old == EMPTY_KEY) {
                 if (bmask) atomicOr(&bmask[rkey >> 5], 1u << (rkey & 31u));
-                unsigned idx = atomicAdd(&st->n_active, 1u);
+                // one counter add for the lanes that claimed a key in this probe step
+                const unsigned grp = __activemask();
+                const int lead = __ffs(grp) - 1, me = (int)(threadIdx.x & 31);
+                unsigned base = 0;
+                if (me == lead) base = atomicAdd(&st->n_active, (unsigned)__popc(grp));
+                const unsigned idx = __shfl_sync(grp, base, lead) + __popc(grp & ((1u << me) - 1u));
                 if ((int64_t)idx < cap) {
                     akey[idx] = rkey;
                     aslot[idx] = (uint32_t)s;

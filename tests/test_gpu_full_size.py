@@ -84,3 +84,46 @@ def test_full_size_parity(oracle_mod, name):
         fb = 16 * U32 * (1 + 27 * wl.dt * vmax / h) * np.abs(F[p]).max()
         assert np.all(np.abs(out["F"][p] - F1) <= 64 * fb + 1e-6)
     sim.close()
+
+
+def test_full_size_ensemble_parity(oracle_mod):
+    """The 64-column ensemble (8,242,000 particles) as bench.py runs it: the
+    active set of three scenarios against the oracle (shifted keys), P2G on
+    sampled nodes and G2P on sampled particles of those scenarios, each from
+    that scenario's own oracle."""
+    import torch
+    ens = W.column_ensemble()
+    sim = mpm.Simulation.from_workload(ens, stream=torch.cuda.current_stream(), device_inputs=True)
+    sim.step(3)
+    st = sim.read_particles()
+    sim.rebuild_active()
+    keys = sim.read_active()
+    sim.p2g()
+    g = sim.read_grid()
+    nodes_all = sparse_node_coords(keys, 4)
+    pitch = (ens.hi[0] // 4) - (ens.lo[0] // 4) + 1
+    c = np.concatenate([[0], np.cumsum(ens.scenario_counts)])
+    rng = np.random.default_rng(11)
+    blocks = mpm.unpack_keys(keys)
+    scen_of_block = (blocks[:, 0] - ens.lo[0] // 4) // pitch
+    for s in rng.choice(len(ens.scenario_counts), 3, replace=False):
+        sl = slice(int(c[s]), int(c[s + 1]))
+        m_wl = W.ensemble_member(ens, s)
+        o = oracle_for(m_wl)
+        x, v, Cm, F = st["x"][sl], st["v"][sl], st["C"][sl], st["F"][sl]
+        # the scenario's active blocks, shifted into its slot along x
+        want = np.asarray(o.active_blocks(x), np.int64).copy()
+        want[:, 0] += s * pitch
+        assert np.array_equal(keys[scen_of_block == s], eq_keys(want))
+        # P2G on sampled nodes of this scenario (local node = global - s * pitch * 4 along x)
+        mine = np.flatnonzero((np.repeat(scen_of_block, 64) == s) & (g["m"] > 0))
+        idx = rng.choice(mine, 32, replace=False)
+        local = nodes_all[idx].copy()
+        local[:, 0] -= s * pitch * 4
+        m, mv, f, af = o.p2g_nodes(local, x, v, Cm, F, m_wl.phi, with_scale=True)
+        mine_m = g["m"][np.repeat(scen_of_block, 64) == s]
+        assert np.all(np.abs(g["m"][idx] - m) <= 1e-6 * np.abs(mine_m).max())
+        mine_mv = g["mv"][np.repeat(scen_of_block, 64) == s]
+        assert np.all(np.abs(g["mv"][idx] - mv) <= 1e-6 * max(np.abs(mine_mv).max(), 1e-30))
+        assert np.all(np.abs(g["f"][idx].astype(np.float64) - f) <= 64 * U32 * af[:, None] + 1e-30)
+    sim.close()
