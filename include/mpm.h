@@ -263,6 +263,30 @@ mpm_status mpm_autotune(mpm_ctx* ctx, int32_t repeats, mpm_tuning* out);
 mpm_status mpm_get_tuning(mpm_ctx* ctx, mpm_tuning* out);
 mpm_status mpm_set_tuning(mpm_ctx* ctx, const mpm_tuning* in);
 
+/* Differentiation: a hand-written adjoint (reverse mode) of one explicit
+ * step, Sec. 4.1, for Neo-Hookean contexts in MPM_DETERMINISTIC mode with
+ * block_size 4 (other contexts: INVALID_ARG).  The paper has no counterpart.
+ *
+ * mpm_state_bytes / mpm_save_state / mpm_load_state copy the context's whole
+ * particle state (internal layout and order, with the stored stress) to or
+ * from a caller device buffer of mpm_state_bytes bytes: checkpoints for
+ * recomputation.  Loading makes the next step repeat, bit for bit, the step
+ * that followed the save.
+ *
+ * mpm_adjoint_step: with the context holding the state S_k of a step k (as
+ * saved before that step), recompute step k's grid and apply the adjoint of
+ * the step.  adj_next (device, read) holds dL/dS_{k+1} and adj_cur (device,
+ * written) receives dL/dS_k, both in particle-id order with 24 floats a
+ * particle: x(3) v(3) C(9) F(9, row-major).  Whatever L depends on through
+ * the stress of S_{k+1} must already be in adj_next's F part (the adjoint of
+ * step k+1 puts it there).  *dE (host) is increased by the step's part of
+ * dL/dE (Young's modulus, nu fixed).  The state is not advanced.
+ * Synchronises. */
+int64_t mpm_state_bytes(const mpm_ctx* ctx);
+mpm_status mpm_save_state(mpm_ctx* ctx, void* dst);
+mpm_status mpm_load_state(mpm_ctx* ctx, const void* src);
+mpm_status mpm_adjoint_step(mpm_ctx* ctx, const float* adj_next, float* adj_cur, double* dE);
+
 /* Static description of a status code; never NULL. */
 const char* mpm_status_string(mpm_status s);
 

@@ -1092,6 +1092,54 @@ mpm_status mpm_set_tuning(mpm_ctx* c, const mpm_tuning* in) {
     return MPM_OK;
 }
 
+int64_t mpm_state_bytes(const mpm_ctx* c) { return c ? (int64_t)sizeof(float) * NF * c->pstride : 0; }
+
+mpm_status mpm_save_state(mpm_ctx* c, void* dst) {
+    if (!c || !dst) return MPM_ERR_INVALID_ARG;
+    if (c->g2p_swapped) {
+        mpm_status s = settle(c);
+        if (s != MPM_OK) return s;
+    }
+    CK(cudaMemcpyAsync(dst, c->ps[c->cur], sizeof(float) * NF * c->pstride, cudaMemcpyDeviceToDevice, c->st));
+    return MPM_OK;
+}
+
+mpm_status mpm_load_state(mpm_ctx* c, const void* src) {
+    if (!c || !src) return MPM_ERR_INVALID_ARG;
+    CK(cudaMemcpyAsync(c->ps[c->cur], src, sizeof(float) * NF * c->pstride, cudaMemcpyDeviceToDevice, c->st));
+    c->phase = 0;
+    c->g2p_swapped = false;
+    return MPM_OK;
+}
+
+mpm_status mpm_adjoint_step(mpm_ctx* c, const float* adj_next, float* adj_cur, double* dE) {
+    if (!c || !adj_next || !adj_cur) return MPM_ERR_INVALID_ARG;
+    if (!c->det || c->B != 4 || c->P.material != MPM_NEOHOOKEAN)
+        return fail(c, MPM_ERR_INVALID_ARG, "the adjoint needs MPM_DETERMINISTIC, block_size 4 and Neo-Hookean");
+    mpm_status s = do_rebuild(c);
+    if (s == MPM_OK) s = do_p2g(c);
+    if (s == MPM_OK) s = do_grid(c);
+    if (s != MPM_OK) return s;
+    const int64_t nodes = c->n_active * 64;
+    if (nodes > c->adj_node_cap) {
+        dfree(c, c->adj_nodes, 0);
+        c->adj_nodes = nullptr;
+        c->adj_node_cap = 0;
+        CK(dalloc(c, (void**)&c->adj_nodes, sizeof(float4) * 3 * nodes));
+        c->adj_node_cap = nodes;
+    }
+    if (!c->adj_dE) CK(dalloc(c, (void**)&c->adj_dE, sizeof(double)));
+    CK(cudaMemsetAsync(c->adj_dE, 0, sizeof(double), c->st));
+    float4* base = c->adj_nodes;
+    CK(launch_adjoint(c, adj_next, adj_cur, base, base + c->adj_node_cap, base + 2 * c->adj_node_cap, c->adj_dE));
+    double h = 0.0;
+    CK(cudaMemcpyAsync(&h, c->adj_dE, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(sync_wait(c));
+    if (dE) *dE += h;
+    c->phase = 0;   // the step is not taken
+    return MPM_OK;
+}
+
 mpm_status mpm_get_stats(mpm_ctx* c, mpm_stats* o) {
     if (!c || !o) return MPM_ERR_INVALID_ARG;
     std::memset(o, 0, sizeof(*o));

@@ -301,6 +301,11 @@ struct mpm_ctx {
     // ensemble
     uint32_t* scen_start = nullptr;
 
+    // adjoint scratch: node adjoints (velocity; mass and momentum; force) and dL/dE
+    float4* adj_nodes = nullptr;
+    int64_t adj_node_cap = 0;
+    double* adj_dE = nullptr;
+
     // status
     mpm::DevStatus* dstat = nullptr;
     mpm::DevStatus* hstat = nullptr;   // pinned
@@ -364,5 +369,9 @@ cudaError_t launch_grid_update(mpm_ctx* c);
 cudaError_t launch_g2p(mpm_ctx* c);
 cudaError_t launch_init_stress(mpm_ctx* c, float* buf);
 cudaError_t launch_step_done(mpm_ctx* c);
+
+// ---- adjoint (adjoint.cu)
+cudaError_t launch_adjoint(mpm_ctx* c, const float* adj_next, float* adj_cur, float4* gvbar, float4* gmbar,
+                           float4* gfbar, double* dE);
 
 }  // namespace mpm

@@ -81,7 +81,8 @@ _lib = None
 EXPORTS = ("mpm_config_default", "mpm_create", "mpm_rebuild_active", "mpm_p2g", "mpm_grid_update", "mpm_g2p",
            "mpm_step", "mpm_read_particles", "mpm_write_particles", "mpm_read_active", "mpm_read_grid",
            "mpm_get_stats", "mpm_status_string", "mpm_last_error", "mpm_destroy", "mpm_active_blocks_noalloc",
-           "mpm_create_ensemble", "mpm_autotune", "mpm_get_tuning", "mpm_set_tuning")
+           "mpm_create_ensemble", "mpm_autotune", "mpm_get_tuning", "mpm_set_tuning", "mpm_state_bytes",
+           "mpm_save_state", "mpm_load_state", "mpm_adjoint_step")
 
 
 def lib():
@@ -97,6 +98,11 @@ def lib():
     L.mpm_config_default.argtypes = [C.POINTER(Config)]
     L.mpm_create.argtypes = [C.POINTER(Config), i64, vp, vp, vp, vp, vp, C.c_int, vp, C.POINTER(vp)]
     L.mpm_autotune.argtypes = [vp, C.c_int32, C.POINTER(Tuning)]
+    L.mpm_state_bytes.argtypes = [vp]
+    L.mpm_state_bytes.restype = C.c_int64
+    L.mpm_save_state.argtypes = [vp, vp]
+    L.mpm_load_state.argtypes = [vp, vp]
+    L.mpm_adjoint_step.argtypes = [vp, vp, vp, C.POINTER(C.c_double)]
     L.mpm_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
     L.mpm_set_tuning.argtypes = [vp, C.POINTER(Tuning)]
     L.mpm_create_ensemble.argtypes = [C.POINTER(Config), C.c_int32, C.POINTER(C.c_int64), vp, vp, vp, vp, vp,
@@ -296,6 +302,24 @@ class Simulation:
     def set_tuning(self, p2g_ctas_per_sm: int, g2p_threads: int, g2p_min_blocks: int):
         t = Tuning(p2g_ctas_per_sm, g2p_threads, g2p_min_blocks, 0, 0.0, 0.0)
         _check(lib().mpm_set_tuning(self.h, C.byref(t)), self.h)
+
+    # ---- checkpoints and the adjoint (device buffers: torch CUDA tensors)
+    def state_bytes(self) -> int:
+        return int(lib().mpm_state_bytes(self.h))
+
+    def save_state(self, dst):
+        _check(lib().mpm_save_state(self.h, C.c_void_p(dst.data_ptr())), self.h)
+
+    def load_state(self, src):
+        _check(lib().mpm_load_state(self.h, C.c_void_p(src.data_ptr())), self.h)
+
+    def adjoint_step(self, adj_next, adj_cur) -> float:
+        """mpm_adjoint_step: adj_next, adj_cur are (n, 24) float32 CUDA tensors
+        (x, v, C, F adjoints in id order); returns this step's dL/dE."""
+        dE = C.c_double(0.0)
+        _check(lib().mpm_adjoint_step(self.h, C.c_void_p(adj_next.data_ptr()), C.c_void_p(adj_cur.data_ptr()),
+                                      C.byref(dE)), self.h)
+        return dE.value
 
     def stats(self):
         s = Stats()

@@ -21,7 +21,7 @@ def native():
 def _declared_functions():
     src = open(os.path.join(ROOT, "include", "mpm.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:mpm_status|const char\s*\*|void)\s+(mpm_\w+)\s*\(", src, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:mpm_status|const char\s*\*|void|int64_t)\s+(mpm_\w+)\s*\(", src, flags=re.M)))
 
 
 def test_header_declares_the_boundary():

@@ -1,0 +1,145 @@
+"""The hand-written adjoint of the explicit step (Neo-Hookean, deterministic
+mode) against FP64 central differences of the oracle: one step for every
+input family (x, v, C, F and Young's modulus E), and a checkpointed rollout
+through the torch.autograd.Function for E and the initial velocities."""
+import numpy as np
+import pytest
+
+from paper_2605_28525_b300 import mpm, workloads as W
+from tests.helpers import oracle_for, small_blob
+
+pytestmark = pytest.mark.gpu
+
+
+def _blob(floor=False):
+    wl, Cm, F = small_blob(n=2000, seed=21, E=1e5, vscale=0.5, cscale=2.0, fscale=0.03, dt=2e-4)
+    if floor:
+        # a Coulomb floor under the blob's lower cells
+        wl.floor_kind, wl.floor_z, wl.floor_mu = W.FLOOR_COULOMB, 12 * wl.dx, 0.3
+    return wl, Cm.reshape(-1, 9), F.reshape(-1, 9)
+
+
+def _oracle(wl, E):
+    import dataclasses
+    return oracle_for(dataclasses.replace(wl, E=E))
+
+
+def _L(out, wts):
+    x, v, Cm, F = out
+    a, b, ca, fa = wts
+    return float((x * a).sum() + (v * b).sum() + (Cm.reshape(-1, 9) * ca).sum() + (F.reshape(-1, 9) * fa).sum())
+
+
+def _pick(x, h, rng, k):
+    """Particles whose cell offsets stay clear of the cell faces (the
+    stencil must not change under the finite differences)."""
+    d = x / h - np.floor(x / h - 0.5)
+    ok = np.all((d > 0.52) & (d < 1.48), axis=1)
+    return rng.choice(np.flatnonzero(ok), k, replace=False)
+
+
+@pytest.mark.parametrize("floor", [False, True])
+def test_one_step_adjoint_matches_fp64_differences(oracle_mod, floor):
+    import torch
+    wl, Cm, F = _blob(floor)
+    n = wl.n
+    rng = np.random.default_rng(5)
+    wts = (rng.standard_normal((n, 3)), rng.standard_normal((n, 3)), rng.standard_normal((n, 9)) * 1e-2,
+           rng.standard_normal((n, 9)))
+    sim = mpm.Simulation(mpm.config_from_workload(wl, flags=mpm.DETERMINISTIC), wl.x, wl.v, Cm, F)
+    adj_next = torch.tensor(np.concatenate(wts, axis=1), dtype=torch.float32, device="cuda")
+    adj_cur = torch.empty_like(adj_next)
+    dE = sim.adjoint_step(adj_next, adj_cur)
+    g = adj_cur.cpu().numpy().astype(np.float64)
+
+    x0, v0, C0, F0 = (a.astype(np.float64) for a in (wl.x, wl.v, Cm, F))
+    o = oracle_for(wl)
+
+    def L_of(x=x0, v=v0, C_=C0, F_=F0, orc=o):
+        return _L(orc.run(x, v, C_, F_, nsteps=1), wts)
+
+    # E
+    dEr = 1e-5 * wl.E
+    fd = (L_of(orc=_oracle(wl, wl.E + dEr)) - L_of(orc=_oracle(wl, wl.E - dEr))) / (2 * dEr)
+    assert abs(dE - fd) <= 1e-3 * abs(fd), (dE, fd)
+    # x, v, C, F of sampled particles
+    ps = _pick(wl.x, wl.dx, rng, 6)
+    fams = {"x": (x0, 0, 3, 1e-5 * wl.dx), "v": (v0, 3, 3, 1e-5), "C": (C0, 6, 9, 1e-4), "F": (F0, 15, 9, 1e-6)}
+    for name, (arr, off, width, eps) in fams.items():
+        got, want = [], []
+        for p in ps:
+            for k in range(width):
+                a1, a2 = arr.copy(), arr.copy()
+                a1[p, k] += eps
+                a2[p, k] -= eps
+                kw1, kw2 = {"x": {}, "v": {}, "C": {}, "F": {}}[name], {}
+                args1 = dict(x=x0, v=v0, C_=C0, F_=F0)
+                args2 = dict(args1)
+                key = {"x": "x", "v": "v", "C": "C_", "F": "F_"}[name]
+                args1[key], args2[key] = a1, a2
+                want.append((L_of(**args1) - L_of(**args2)) / (2 * eps))
+                got.append(g[p, off + k])
+        got, want = np.array(got), np.array(want)
+        assert np.abs(got - want).max() <= 1e-3 * np.abs(want).max(), (name, got, want)
+
+
+def test_checkpointed_rollout_gradient(oracle_mod):
+    import torch
+    from paper_2605_28525_b300 import adjoint
+    wl, Cm, F = _blob()
+    n, K = wl.n, 24
+    rng = np.random.default_rng(8)
+    cx, cv = rng.standard_normal((n, 3)), rng.standard_normal((n, 3))
+    C_d = torch.tensor(Cm, device="cuda")
+    F_d = torch.tensor(F, device="cuda")
+
+    def make_sim(E, x0, v0):
+        import dataclasses
+        cfg = mpm.config_from_workload(dataclasses.replace(wl, E=E), flags=mpm.DETERMINISTIC)
+        return mpm.Simulation(cfg, x0, v0, C_d, F_d)
+
+    grads = []
+    for every in (7, K):
+        E = torch.tensor(wl.E, dtype=torch.float64, requires_grad=True)
+        x0 = torch.tensor(wl.x, device="cuda", requires_grad=True)
+        v0 = torch.tensor(wl.v, device="cuda", requires_grad=True)
+        xK, vK = adjoint.Rollout.apply(E, x0, v0, make_sim, K, every)
+        loss = (xK.double() * torch.tensor(cx, device="cuda")).sum() + \
+               (vK.double() * torch.tensor(cv, device="cuda")).sum()
+        loss.backward()
+        grads.append((float(E.grad), v0.grad.cpu().numpy().astype(np.float64), loss.item()))
+    # checkpointing changes nothing but the float-atomic order of the node adjoints
+    assert abs(grads[0][0] - grads[1][0]) <= 1e-5 * abs(grads[1][0])
+    assert np.allclose(grads[0][1], grads[1][1], rtol=1e-4, atol=1e-6 * np.abs(grads[1][1]).max())
+
+    x0d, v0d, C0d, F0d = (a.astype(np.float64) for a in (wl.x, wl.v, Cm, F))
+
+    def L_of(E=wl.E, v=v0d):
+        x, vv, _, _ = _oracle(wl, E).run(x0d, v, C0d, F0d, nsteps=K)
+        return float((x * cx).sum() + (vv * cv).sum())
+
+    dEr = 1e-5 * wl.E
+    fd = (L_of(E=wl.E + dEr) - L_of(E=wl.E - dEr)) / (2 * dEr)
+    assert abs(grads[0][0] - fd) <= 1e-3 * abs(fd), (grads[0][0], fd)
+    got, want = [], []
+    for p in _pick(wl.x, wl.dx, rng, 4):
+        for k in range(3):
+            a1, a2 = v0d.copy(), v0d.copy()
+            a1[p, k] += 1e-5
+            a2[p, k] -= 1e-5
+            want.append((L_of(v=a1) - L_of(v=a2)) / 2e-5)
+            got.append(grads[0][1][p, k])
+    got, want = np.array(got), np.array(want)
+    assert np.abs(got - want).max() <= 1e-3 * np.abs(want).max(), (got, want)
+
+
+def test_adjoint_refuses_unsupported_contexts(oracle_mod):
+    import torch
+    wl, Cm, F = _blob()
+    adj = torch.zeros(wl.n, 24, device="cuda")
+    for flags, mat in [(0, W.NEOHOOKEAN), (mpm.DETERMINISTIC, W.DRUCKER_PRAGER)]:
+        wl.material = mat
+        sim = mpm.Simulation(mpm.config_from_workload(wl, flags=flags), wl.x, wl.v, Cm, F)
+        with pytest.raises(mpm.MpmError) as e:
+            sim.adjoint_step(adj, torch.empty_like(adj))
+        assert e.value.status == mpm.ERR_INVALID_ARG
