@@ -264,7 +264,8 @@ mpm_status mpm_get_tuning(mpm_ctx* ctx, mpm_tuning* out);
 mpm_status mpm_set_tuning(mpm_ctx* ctx, const mpm_tuning* in);
 
 /* Differentiation: a hand-written adjoint (reverse mode) of one explicit
- * step, Sec. 4.1, for Neo-Hookean contexts in MPM_DETERMINISTIC mode with
+ * step, Sec. 4.1, with the Neo-Hookean stress or the Drucker-Prager return
+ * map and Hencky stress, for contexts in MPM_DETERMINISTIC mode with
  * block_size 4 (other contexts: INVALID_ARG).  The paper has no counterpart.
  *
  * mpm_state_bytes / mpm_save_state / mpm_load_state copy the context's whole
@@ -279,13 +280,14 @@ mpm_status mpm_set_tuning(mpm_ctx* ctx, const mpm_tuning* in);
  * written) receives dL/dS_k, both in particle-id order with 24 floats a
  * particle: x(3) v(3) C(9) F(9, row-major).  Whatever L depends on through
  * the stress of S_{k+1} must already be in adj_next's F part (the adjoint of
- * step k+1 puts it there).  *dE (host) is increased by the step's part of
- * dL/dE (Young's modulus, nu fixed).  The state is not advanced.
- * Synchronises. */
+ * step k+1 puts it there).  *dE and *dphi (host, nullable) are increased by
+ * the step's part of dL/dE (Young's modulus, nu fixed) and, for
+ * Drucker-Prager, of dL/dphi (degrees; every particle's friction angle moved
+ * by the same amount).  The state is not advanced.  Synchronises. */
 int64_t mpm_state_bytes(const mpm_ctx* ctx);
 mpm_status mpm_save_state(mpm_ctx* ctx, void* dst);
 mpm_status mpm_load_state(mpm_ctx* ctx, const void* src);
-mpm_status mpm_adjoint_step(mpm_ctx* ctx, const float* adj_next, float* adj_cur, double* dE);
+mpm_status mpm_adjoint_step(mpm_ctx* ctx, const float* adj_next, float* adj_cur, double* dE, double* dphi);
 
 /* Static description of a status code; never NULL. */
 const char* mpm_status_string(mpm_status s);

@@ -37,11 +37,12 @@ def rollout(sim: "mpm.Simulation", nsteps: int, every: int):
 
 
 def gradient(sim: "mpm.Simulation", ckpts, nsteps: int, every: int, adj_final: torch.Tensor):
-    """dL/d(initial state) (n, 24) and dL/dE, given dL/d(final state)."""
+    """dL/d(initial state) (n, 24), dL/dE and dL/dphi (Drucker-Prager; phi in
+    degrees, every particle's angle moved together), given dL/d(final state)."""
     nbytes = sim.state_bytes()
     adj_next = adj_final.contiguous().clone()
     adj_cur = torch.empty_like(adj_next)
-    dE = 0.0
+    dE = dphi = 0.0
     for s in range(len(ckpts) - 1, -1, -1):
         k0 = s * every
         k = min(every, nsteps - k0)
@@ -55,9 +56,11 @@ def gradient(sim: "mpm.Simulation", ckpts, nsteps: int, every: int, adj_final: t
                 sim.step(1)
         for j in range(k - 1, -1, -1):
             sim.load_state(states[j])
-            dE += sim.adjoint_step(adj_next, adj_cur)
+            e, ph = sim.adjoint_step(adj_next, adj_cur)
+            dE += e
+            dphi += ph
             adj_next, adj_cur = adj_cur, adj_next
-    return adj_next, dE
+    return adj_next, dE, dphi
 
 
 class Rollout(torch.autograd.Function):
@@ -79,6 +82,6 @@ class Rollout(torch.autograd.Function):
         adj[:, 0:3] = gx
         if gv is not None:
             adj[:, 3:6] = gv
-        g0, dE = gradient(ctx.sim, ctx.ckpts, ctx.nsteps, ctx.every, adj)
+        g0, dE, _ = gradient(ctx.sim, ctx.ckpts, ctx.nsteps, ctx.every, adj)
         ctx.sim.close()
         return (torch.tensor(dE, dtype=torch.float64), g0[:, 0:3].clone(), g0[:, 3:6].clone(), None, None, None)

@@ -5,7 +5,9 @@
 //   grid  v^_n = p_n / m_n + dt (f_n / m_n + g), then the boundary conditions
 //   G2P   v_p' = sum_n N v_n,  C_p' = 4/h^2 sum_n N v_n (x_n - x_p)^T,
 //         F_p' = (I + dt sum_n v_n grad N^T) F_p,  x_p' = x_p + dt v_p',
-//         tau_p' = mu (F' F'^T - I) + lambda ln J' I   (Neo-Hookean)
+//         tau_p' = mu (F' F'^T - I) + lambda ln J' I   (Neo-Hookean), or for
+//         Drucker-Prager F' = U exp(H(ln S)) V^T (the return map of F_tr =
+//         U S V^T) and tau' = U diag(2 mu H + lambda tr H) U^T
 //
 // Given the adjoint of the state after the step (x', v', C', F'; the stress
 // the next step's P2G reads is folded into F' by that step's adjoint), the
@@ -22,6 +24,16 @@
 //                sticky, slip and Coulomb rules) and the momentum division
 //   k_adj_p2g    per particle: adjoint of P2G gathered from the 27 nodes,
 //                then of the stress; dL/dE summed in double
+//
+// The Drucker-Prager return map and the Hencky stress are isotropic functions
+// of F.  Their adjoints come from the SVD differential: with P = U^T dF V,
+// a function U diag(g(S)) V^T has the differential U K V^T with
+// K_ii = sum_j dg_i/dS_j P_jj and, for i != j, K_ij = a P_ij + b P_ji,
+// a, b = ((g_i - g_j)/(S_i - S_j) +- (g_i + g_j)/(S_i + S_j)) / 2, and the
+// stress U diag(s) U^T has off-diagonal terms
+// (s_j - s_i)/(S_j - S_i) (S_j P_ij + S_i P_ji)/(S_i + S_j).  The divided
+// differences are taken in FP64 on an FP64 SVD of the FP32 state, with their
+// limits where two singular values coincide.
 #include <algorithm>
 
 #include "mpm_internal.cuh"
@@ -113,14 +125,236 @@ __device__ __forceinline__ void particle_geometry(const Params& P, const float x
     }
 }
 
-template <bool DENSE>
+// ---------------------------------------------------------- FP64 SVD
+
+// One Jacobi rotation of the symmetric S in the (p, q) plane, accumulated
+// in the columns of V (classical formulas, t = the smaller root).
+__device__ void djacobi(double S[3][3], double V[3][3], int p, int q) {
+    const double spq = S[p][q];
+    if (fabs(spq) <= 1e-300) return;
+    const double theta = (S[q][q] - S[p][p]) / (2.0 * spq);
+    const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+    const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+    for (int k = 0; k < 3; ++k) {
+        const double skp = S[k][p], skq = S[k][q];
+        S[k][p] = c * skp - s * skq;
+        S[k][q] = s * skp + c * skq;
+    }
+    for (int k = 0; k < 3; ++k) {
+        const double spk = S[p][k], sqk = S[q][k];
+        S[p][k] = c * spk - s * sqk;
+        S[q][k] = s * spk + c * sqk;
+    }
+    for (int k = 0; k < 3; ++k) {
+        const double vkp = V[k][p], vkq = V[k][q];
+        V[k][p] = c * vkp - s * vkq;
+        V[k][q] = s * vkp + c * vkq;
+    }
+}
+
+// F = U diag(sg) V^T with U, V rotations and sg descending (sg[2] carries
+// the sign of det F); Jacobi eigenanalysis of F^T F for V, then U by
+// orthonormalising F V.  False for a rank-deficient F.
+__device__ bool dsvd3(const float Ff[9], double U[3][3], double sg[3], double V[3][3]) {
+    double F[9], S[3][3];
+    for (int k = 0; k < 9; ++k) F[k] = (double)Ff[k];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            S[i][j] = F[i] * F[j] + F[3 + i] * F[3 + j] + F[6 + i] * F[6 + j];
+            V[i][j] = i == j ? 1.0 : 0.0;
+        }
+    for (int sweep = 0; sweep < 12; ++sweep) {
+        djacobi(S, V, 0, 1);
+        djacobi(S, V, 0, 2);
+        djacobi(S, V, 1, 2);
+    }
+    double ev[3] = {S[0][0], S[1][1], S[2][2]};
+    for (int a = 0; a < 2; ++a)
+        for (int b = a + 1; b < 3; ++b)
+            if (ev[a] < ev[b]) {
+                const double t = ev[a];
+                ev[a] = ev[b];
+                ev[b] = t;
+                for (int k = 0; k < 3; ++k) {
+                    const double tv = V[k][a];
+                    V[k][a] = V[k][b];
+                    V[k][b] = tv;
+                }
+            }
+    const double dv = V[0][0] * (V[1][1] * V[2][2] - V[1][2] * V[2][1]) -
+                      V[0][1] * (V[1][0] * V[2][2] - V[1][2] * V[2][0]) +
+                      V[0][2] * (V[1][0] * V[2][1] - V[1][1] * V[2][0]);
+    if (dv < 0.0)
+        for (int k = 0; k < 3; ++k) V[k][2] = -V[k][2];
+    double Bc[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Bc[i][j] = F[i * 3] * V[0][j] + F[i * 3 + 1] * V[1][j] + F[i * 3 + 2] * V[2][j];
+    const double n0 = sqrt(Bc[0][0] * Bc[0][0] + Bc[1][0] * Bc[1][0] + Bc[2][0] * Bc[2][0]);
+    if (!(n0 > 0.0)) return false;
+    const double u0[3] = {Bc[0][0] / n0, Bc[1][0] / n0, Bc[2][0] / n0};
+    const double d01 = u0[0] * Bc[0][1] + u0[1] * Bc[1][1] + u0[2] * Bc[2][1];
+    double u1[3] = {Bc[0][1] - d01 * u0[0], Bc[1][1] - d01 * u0[1], Bc[2][1] - d01 * u0[2]};
+    const double n1 = sqrt(u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
+    if (!(n1 > 0.0)) return false;
+    for (int k = 0; k < 3; ++k) u1[k] /= n1;
+    const double u2[3] = {u0[1] * u1[2] - u0[2] * u1[1], u0[2] * u1[0] - u0[0] * u1[2], u0[0] * u1[1] - u0[1] * u1[0]};
+    sg[0] = n0;
+    sg[1] = n1;
+    sg[2] = u2[0] * Bc[0][2] + u2[1] * Bc[1][2] + u2[2] * Bc[2][2];
+    for (int i = 0; i < 3; ++i) {
+        U[i][0] = u0[i];
+        U[i][1] = u1[i];
+        U[i][2] = u2[i];
+    }
+    return true;
+}
+
+// (a_i - a_j) / (x_i - x_j), or lim when the x are (nearly) equal.
+__device__ __forceinline__ double ddiff(double ai, double aj, double xi, double xj, double lim) {
+    const double dx = xi - xj;
+    return fabs(dx) > 1e-10 * fmax(fabs(xi), fabs(xj)) ? (ai - aj) / dx : lim;
+}
+
+// The forward's Drucker-Prager return map in principal stretches:
+// g_i = exp(H_i(ln sg)), its Jacobian Jg[i][j] = dg_i/dsg_j and dg/dalpha.
+__device__ void dp_map(const double sg[3], double alpha, double kappa, double g[3], double Jg[3][3],
+                       double dga[3]) {
+    double e[3], dev[3];
+    for (int k = 0; k < 3; ++k) e[k] = log(sg[k]);
+    const double tr = e[0] + e[1] + e[2];
+    for (int k = 0; k < 3; ++k) dev[k] = e[k] - tr / 3.0;
+    const double nd = sqrt(dev[0] * dev[0] + dev[1] * dev[1] + dev[2] * dev[2]);
+    const double dgam = nd + kappa * tr * alpha;
+    double H[3], dH[3][3], dHa[3];
+    if (tr >= 0.0) {                      // tip of the cone
+        for (int i = 0; i < 3; ++i) {
+            H[i] = 0.0;
+            dHa[i] = 0.0;
+            for (int j = 0; j < 3; ++j) dH[i][j] = 0.0;
+        }
+    } else if (dgam <= 0.0) {             // inside the cone
+        for (int i = 0; i < 3; ++i) {
+            H[i] = e[i];
+            dHa[i] = 0.0;
+            for (int j = 0; j < 3; ++j) dH[i][j] = i == j ? 1.0 : 0.0;
+        }
+    } else {                              // onto the cone: H = tr/3 - beta dev
+        const double beta = kappa * alpha * tr / nd;
+        for (int i = 0; i < 3; ++i) {
+            H[i] = tr / 3.0 - beta * dev[i];
+            dHa[i] = -(kappa * tr / nd) * dev[i];
+            for (int j = 0; j < 3; ++j) {
+                const double dbeta = kappa * alpha * (1.0 / nd - tr * dev[j] / (nd * nd * nd));
+                dH[i][j] = 1.0 / 3.0 - (dbeta * dev[i] + beta * ((i == j ? 1.0 : 0.0) - 1.0 / 3.0));
+            }
+        }
+    }
+    for (int i = 0; i < 3; ++i) {
+        g[i] = exp(H[i]);
+        dga[i] = g[i] * dHa[i];
+        for (int j = 0; j < 3; ++j) Jg[i][j] = g[i] * dH[i][j] / sg[j];
+    }
+}
+
+// Fbar_tr = (d returnmap / dF at F_tr)^T Fbar' and dL/dalpha.  False if F_tr
+// has no usable SVD (the forward step would have failed).
+__device__ bool dp_map_adjoint(const float Ftr[9], double alpha, double kappa, const float Fb[9], float Fb_tr[9],
+                               double* abar) {
+    double U[3][3], sg[3], V[3][3];
+    if (!dsvd3(Ftr, U, sg, V) || !(sg[2] > 0.0)) return false;
+    double g[3], Jg[3][3], dga[3];
+    dp_map(sg, alpha, kappa, g, Jg, dga);
+    double Gb[3][3];   // U^T Fbar V
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double v = 0.0;
+            for (int k = 0; k < 3; ++k)
+                for (int l = 0; l < 3; ++l) v += U[k][i] * (double)Fb[k * 3 + l] * V[l][j];
+            Gb[i][j] = v;
+        }
+    double M[3][3];
+    for (int i = 0; i < 3; ++i) {
+        double v = 0.0;
+        for (int j = 0; j < 3; ++j) v += Gb[j][j] * Jg[j][i];
+        M[i][i] = v;
+    }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            if (i == j) continue;
+            const double lim = 0.5 * ((Jg[i][i] - Jg[j][i]) + (Jg[j][j] - Jg[i][j]));
+            const double q = ddiff(g[i], g[j], sg[i], sg[j], lim);
+            const double r = (g[i] + g[j]) / (sg[i] + sg[j]);
+            M[i][j] = 0.5 * (q + r) * Gb[i][j] + 0.5 * (q - r) * Gb[j][i];
+        }
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double v = 0.0;
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) v += U[a][i] * M[i][j] * V[b][j];
+            Fb_tr[a * 3 + b] = (float)v;
+        }
+    *abar = Gb[0][0] * dga[0] + Gb[1][1] * dga[1] + Gb[2][2] * dga[2];
+    return true;
+}
+
+// Hencky stress tau = U diag(2 mu ln sg + lambda sum ln sg) U^T of the
+// elastic F: adds (dtau/dF)^T taubar to Fbar; returns taubar : dtau/dE.
+__device__ double hencky_adjoint(const float Ff[9], const float tb[9], double mu, double la, double dmu, double dla,
+                                 float Fb[9]) {
+    double U[3][3], sg[3], V[3][3];
+    if (!dsvd3(Ff, U, sg, V) || !(sg[2] > 0.0)) return 0.0;
+    const double ls[3] = {log(sg[0]), log(sg[1]), log(sg[2])};
+    const double trl = ls[0] + ls[1] + ls[2];
+    double T[3][3];   // U^T taubar U
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double v = 0.0;
+            for (int k = 0; k < 3; ++k)
+                for (int l = 0; l < 3; ++l) v += U[k][i] * (double)tb[k * 3 + l] * U[l][j];
+            T[i][j] = v;
+        }
+    double M[3][3];
+    for (int i = 0; i < 3; ++i) {
+        double v = 0.0;   // sum_j T_jj ds_j/dsg_i, ds_j/dsg_i = (2 mu delta_ij + lambda) / sg_i
+        for (int j = 0; j < 3; ++j) v += T[j][j] * ((i == j ? 2.0 * mu : 0.0) + la) / sg[i];
+        M[i][i] = v;
+    }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            if (i == j) continue;
+            // (s_j - s_i) / (sg_j - sg_i) = 2 mu (ln sg_j - ln sg_i) / (sg_j - sg_i)
+            const double c = 2.0 * mu * ddiff(ls[j], ls[i], sg[j], sg[i], 2.0 / (sg[i] + sg[j]));
+            M[i][j] = c * sg[j] * (T[i][j] + T[j][i]) / (sg[i] + sg[j]);
+        }
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double v = 0.0;
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) v += U[a][i] * M[i][j] * V[b][j];
+            Fb[a * 3 + b] += (float)v;
+        }
+    return 2.0 * (T[0][0] * ls[0] + T[1][1] * ls[1] + T[2][2] * ls[2]) * dmu + (T[0][0] + T[1][1] + T[2][2]) * trl * dla;
+}
+
+// d alpha / d phi (phi in degrees) for alpha = sqrt(2/3) 2 sin phi / (3 - sin phi).
+__device__ __forceinline__ double dalpha_dphi(double alpha) {
+    const double k = 0.816496580927726 * 2.0;     // sqrt(2/3) * 2
+    const double sp = 3.0 * alpha / (k + alpha);  // sin phi
+    const double cp = sqrt(fmax(0.0, 1.0 - sp * sp));
+    return k * 3.0 * cp / ((3.0 - sp) * (3.0 - sp)) * (3.141592653589793 / 180.0);
+}
+
+template <bool DENSE, int MAT>
 __global__ void __launch_bounds__(128) k_adj_g2p(const float* __restrict__ ps, int64_t stride,
                                                  const uint32_t* __restrict__ perm, const uint32_t* __restrict__ skey,
                                                  int64_t n, const int* __restrict__ nbr, Params P,
                                                  const float4* __restrict__ gv, const float* __restrict__ adj_next,
-                                                 float* __restrict__ adj_cur, float4* __restrict__ gvbar) {
+                                                 float* __restrict__ adj_cur, float4* __restrict__ gvbar,
+                                                 double kappa, double* __restrict__ dphi) {
+    __shared__ double red[4];
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    double phi_part = 0.0;
+    if (i < n) {
     const int64_t p = perm[i];
     const int64_t id = (int64_t)__float_as_uint(ps[PID * stride + p]);
     int q[8];
@@ -158,7 +392,27 @@ __global__ void __launch_bounds__(128) k_adj_g2p(const float* __restrict__ ps, i
 #pragma unroll
                     for (int s = 0; s < 3; ++s) L[r * 3 + s] += v3[r] * nw.g[s];
             }
-    // Lbar = dt F'bar F^T
+    if (MAT == MPM_DRUCKER_PRAGER) {
+        // F' is the return map of F_tr = (I + dt L) F: Fbar_tr = (dF'/dF_tr)^T Fbar'
+        float Ftr[9], Fbt[9];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int s = 0; s < 3; ++s) {
+                float v = F[r * 3 + s];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) v += P.dt * L[r * 3 + k] * F[k * 3 + s];
+                Ftr[r * 3 + s] = v;
+            }
+        double abar = 0.0;
+        const double alpha = (double)ps[PPHI * stride + p];
+        if (dp_map_adjoint(Ftr, alpha, kappa, Fb_n, Fbt, &abar)) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) Fb_n[k] = Fbt[k];
+            phi_part = abar * dalpha_dphi(alpha);
+        }
+    }
+    // Lbar = dt F_tr-bar F^T
     float Lb[9];
 #pragma unroll
     for (int r = 0; r < 3; ++r)
@@ -217,6 +471,13 @@ __global__ void __launch_bounds__(128) k_adj_g2p(const float* __restrict__ ps, i
             for (int k = 0; k < 3; ++k) v += P.dt * L[k * 3 + r] * Fb_n[k * 3 + s];
             ac[AF + r * 3 + s] = v;
         }
+    }
+    if (MAT == MPM_DRUCKER_PRAGER) {   // block sum of dL/dphi, one double atomic per block
+        for (int o = 16; o > 0; o >>= 1) phi_part += __shfl_down_sync(0xffffffffu, phi_part, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = phi_part;
+        __syncthreads();
+        if (threadIdx.x == 0) atomicAdd(dphi, red[0] + red[1] + red[2] + red[3]);
+    }
 }
 
 // Jacobian-transpose of the Coulomb rule at velocity v (before the rule)
@@ -345,7 +606,7 @@ __global__ void __launch_bounds__(256) k_adj_grid(int64_t cap, const DevStatus* 
     }
 }
 
-template <bool DENSE>
+template <bool DENSE, int MAT>
 __global__ void __launch_bounds__(128) k_adj_p2g(const float* __restrict__ ps, int64_t stride,
                                                  const uint32_t* __restrict__ perm, const uint32_t* __restrict__ skey,
                                                  int64_t n, const int* __restrict__ nbr, Params P,
@@ -409,24 +670,7 @@ __global__ void __launch_bounds__(128) k_adj_p2g(const float* __restrict__ ps, i
                         }
                     }
                 }
-        // stress: tau = mu (F F^T - I) + lambda ln J I
-        //   Fbar += mu (taubar + taubar^T) F + lambda tr(taubar) F^-T
-        const float J = F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) +
-                        F[2] * (F[3] * F[7] - F[4] * F[6]);
-        const float cof[9] = {F[4] * F[8] - F[5] * F[7], F[5] * F[6] - F[3] * F[8], F[3] * F[7] - F[4] * F[6],
-                              F[2] * F[7] - F[1] * F[8], F[0] * F[8] - F[2] * F[6], F[1] * F[6] - F[0] * F[7],
-                              F[1] * F[5] - F[2] * F[4], F[2] * F[3] - F[0] * F[5], F[0] * F[4] - F[1] * F[3]};
-        const float trb = tb[0] + tb[4] + tb[8];
         float* ac = adj_cur + id * ANF;
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-#pragma unroll
-            for (int s = 0; s < 3; ++s) {
-                float sym = 0.f;
-#pragma unroll
-                for (int k = 0; k < 3; ++k) sym += (tb[r * 3 + k] + tb[k * 3 + r]) * F[k * 3 + s];
-                ac[AF + r * 3 + s] += P.mu * sym + P.lambda * trb * cof[r * 3 + s] / J;
-            }
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             ac[AX + k] += xb[k];
@@ -434,17 +678,44 @@ __global__ void __launch_bounds__(128) k_adj_p2g(const float* __restrict__ ps, i
         }
 #pragma unroll
         for (int k = 0; k < 9; ++k) ac[AC + k] += Cb[k];
-        // dE: taubar : (F F^T - I) dmu/dE + tr(taubar) ln J dlambda/dE
-        double bb = 0.0;
+        if (MAT == MPM_DRUCKER_PRAGER) {
+            // Hencky stress of the stored elastic F
+            float Fbs[9];
 #pragma unroll
-        for (int r = 0; r < 3; ++r)
+            for (int k = 0; k < 9; ++k) Fbs[k] = ac[AF + k];
+            e_part = hencky_adjoint(F, tb, (double)P.mu, (double)P.lambda, dmu_dE, dla_dE, Fbs);
 #pragma unroll
-            for (int s = 0; s < 3; ++s) {
-                const double ffT = (double)F[r * 3 + 0] * F[s * 3 + 0] + (double)F[r * 3 + 1] * F[s * 3 + 1] +
-                                   (double)F[r * 3 + 2] * F[s * 3 + 2] - (r == s ? 1.0 : 0.0);
-                bb += (double)tb[r * 3 + s] * ffT;
-            }
-        e_part = bb * dmu_dE + (double)trb * log((double)J) * dla_dE;
+            for (int k = 0; k < 9; ++k) ac[AF + k] = Fbs[k];
+        } else {
+            // Neo-Hookean: tau = mu (F F^T - I) + lambda ln J I,
+            //   Fbar += mu (taubar + taubar^T) F + lambda tr(taubar) F^-T
+            const float J = F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) +
+                            F[2] * (F[3] * F[7] - F[4] * F[6]);
+            const float cof[9] = {F[4] * F[8] - F[5] * F[7], F[5] * F[6] - F[3] * F[8], F[3] * F[7] - F[4] * F[6],
+                                  F[2] * F[7] - F[1] * F[8], F[0] * F[8] - F[2] * F[6], F[1] * F[6] - F[0] * F[7],
+                                  F[1] * F[5] - F[2] * F[4], F[2] * F[3] - F[0] * F[5], F[0] * F[4] - F[1] * F[3]};
+            const float trb = tb[0] + tb[4] + tb[8];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int s = 0; s < 3; ++s) {
+                    float sym = 0.f;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) sym += (tb[r * 3 + k] + tb[k * 3 + r]) * F[k * 3 + s];
+                    ac[AF + r * 3 + s] += P.mu * sym + P.lambda * trb * cof[r * 3 + s] / J;
+                }
+            // dE: taubar : (F F^T - I) dmu/dE + tr(taubar) ln J dlambda/dE
+            double bb = 0.0;
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int s = 0; s < 3; ++s) {
+                    const double ffT = (double)F[r * 3 + 0] * F[s * 3 + 0] + (double)F[r * 3 + 1] * F[s * 3 + 1] +
+                                       (double)F[r * 3 + 2] * F[s * 3 + 2] - (r == s ? 1.0 : 0.0);
+                    bb += (double)tb[r * 3 + s] * ffT;
+                }
+            e_part = bb * dmu_dE + (double)trb * log((double)J) * dla_dE;
+        }
     }
     // block sum, one double atomic per block
     for (int o = 16; o > 0; o >>= 1) e_part += __shfl_down_sync(0xffffffffu, e_part, o);
@@ -460,7 +731,7 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 // Adjoint of the step whose grid the phase calls just built (rebuild, P2G
 // and grid update on the saved state, deterministic mode, B = 4).
 cudaError_t launch_adjoint(mpm_ctx* c, const float* adj_next, float* adj_cur, float4* gvbar, float4* gmbar,
-                           float4* gfbar, double* dE) {
+                           float4* gfbar, double* dE, double* dphi) {
     const float* ps = c->ps[c->cur];
     const uint32_t* perm = c->pval[c->sorted_sel];
     const uint32_t* skey = c->pkey[c->sorted_sel];
@@ -470,22 +741,26 @@ cudaError_t launch_adjoint(mpm_ctx* c, const float* adj_next, float* adj_cur, fl
     const unsigned g = blocks_for(c->n, 128);
     const double nu = c->cfg.nu;
     const double dmu = 1.0 / (2.0 * (1.0 + nu)), dla = nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+    const double kappa = (3.0 * (double)c->P.lambda + 2.0 * (double)c->P.mu) / (2.0 * (double)c->P.mu);
     const unsigned gg = (unsigned)std::min<int64_t>(blocks_for(nodes, 256), 148 * 16);
+#define MPM_ADJ(D_, M_)                                                                                           \
+    do {                                                                                                          \
+        k_adj_g2p<D_, M_><<<g, 128, 0, c->st>>>(ps, c->pstride, perm, skey, c->n, c->nbr, c->P, c->gv, adj_next,  \
+                                                adj_cur, gvbar, kappa, dphi);                                    \
+        k_adj_grid<D_><<<gg, 256, 0, c->st>>>(c->live_cap, c->dstat, c->P, c->bcoord, c->gmv, c->gf, gvbar, gmbar, \
+                                              gfbar);                                                             \
+        k_adj_p2g<D_, M_><<<g, 128, 0, c->st>>>(ps, c->pstride, perm, skey, c->n, c->nbr, c->P, gmbar, gfbar,     \
+                                                adj_cur, dmu, dla, dE);                                          \
+    } while (0)
+    const bool dp = c->P.material == MPM_DRUCKER_PRAGER;
     if (c->dense) {
-        k_adj_g2p<true><<<g, 128, 0, c->st>>>(ps, c->pstride, perm, skey, c->n, c->nbr, c->P, c->gv, adj_next, adj_cur,
-                                              gvbar);
-        k_adj_grid<true><<<gg, 256, 0, c->st>>>(c->live_cap, c->dstat, c->P, c->bcoord, c->gmv, c->gf, gvbar, gmbar,
-                                                gfbar);
-        k_adj_p2g<true><<<g, 128, 0, c->st>>>(ps, c->pstride, perm, skey, c->n, c->nbr, c->P, gmbar, gfbar, adj_cur,
-                                              dmu, dla, dE);
+        if (dp) MPM_ADJ(true, MPM_DRUCKER_PRAGER);
+        else MPM_ADJ(true, MPM_NEOHOOKEAN);
     } else {
-        k_adj_g2p<false><<<g, 128, 0, c->st>>>(ps, c->pstride, perm, skey, c->n, c->nbr, c->P, c->gv, adj_next,
-                                               adj_cur, gvbar);
-        k_adj_grid<false><<<gg, 256, 0, c->st>>>(c->live_cap, c->dstat, c->P, c->bcoord, c->gmv, c->gf, gvbar, gmbar,
-                                                 gfbar);
-        k_adj_p2g<false><<<g, 128, 0, c->st>>>(ps, c->pstride, perm, skey, c->n, c->nbr, c->P, gmbar, gfbar, adj_cur,
-                                               dmu, dla, dE);
+        if (dp) MPM_ADJ(false, MPM_DRUCKER_PRAGER);
+        else MPM_ADJ(false, MPM_NEOHOOKEAN);
     }
+#undef MPM_ADJ
     c->launches += 3;
     return cudaGetLastError();
 }

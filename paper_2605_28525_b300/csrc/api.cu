@@ -1112,10 +1112,10 @@ mpm_status mpm_load_state(mpm_ctx* c, const void* src) {
     return MPM_OK;
 }
 
-mpm_status mpm_adjoint_step(mpm_ctx* c, const float* adj_next, float* adj_cur, double* dE) {
+mpm_status mpm_adjoint_step(mpm_ctx* c, const float* adj_next, float* adj_cur, double* dE, double* dphi) {
     if (!c || !adj_next || !adj_cur) return MPM_ERR_INVALID_ARG;
-    if (!c->det || c->B != 4 || c->P.material != MPM_NEOHOOKEAN)
-        return fail(c, MPM_ERR_INVALID_ARG, "the adjoint needs MPM_DETERMINISTIC, block_size 4 and Neo-Hookean");
+    if (!c->det || c->B != 4)
+        return fail(c, MPM_ERR_INVALID_ARG, "the adjoint needs MPM_DETERMINISTIC and block_size 4");
     mpm_status s = do_rebuild(c);
     if (s == MPM_OK) s = do_p2g(c);
     if (s == MPM_OK) s = do_grid(c);
@@ -1128,14 +1128,16 @@ mpm_status mpm_adjoint_step(mpm_ctx* c, const float* adj_next, float* adj_cur, d
         CK(dalloc(c, (void**)&c->adj_nodes, sizeof(float4) * 3 * nodes));
         c->adj_node_cap = nodes;
     }
-    if (!c->adj_dE) CK(dalloc(c, (void**)&c->adj_dE, sizeof(double)));
-    CK(cudaMemsetAsync(c->adj_dE, 0, sizeof(double), c->st));
+    if (!c->adj_dE) CK(dalloc(c, (void**)&c->adj_dE, 2 * sizeof(double)));
+    CK(cudaMemsetAsync(c->adj_dE, 0, 2 * sizeof(double), c->st));
     float4* base = c->adj_nodes;
-    CK(launch_adjoint(c, adj_next, adj_cur, base, base + c->adj_node_cap, base + 2 * c->adj_node_cap, c->adj_dE));
-    double h = 0.0;
-    CK(cudaMemcpyAsync(&h, c->adj_dE, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(launch_adjoint(c, adj_next, adj_cur, base, base + c->adj_node_cap, base + 2 * c->adj_node_cap, c->adj_dE,
+                      c->adj_dE + 1));
+    double h[2] = {0.0, 0.0};
+    CK(cudaMemcpyAsync(h, c->adj_dE, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
     CK(sync_wait(c));
-    if (dE) *dE += h;
+    if (dE) *dE += h[0];
+    if (dphi) *dphi += h[1];
     c->phase = 0;   // the step is not taken
     return MPM_OK;
 }

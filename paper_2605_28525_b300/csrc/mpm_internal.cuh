@@ -304,7 +304,7 @@ struct mpm_ctx {
     // adjoint scratch: node adjoints (velocity; mass and momentum; force) and dL/dE
     float4* adj_nodes = nullptr;
     int64_t adj_node_cap = 0;
-    double* adj_dE = nullptr;
+    double* adj_dE = nullptr;   // [dL/dE, dL/dphi]
 
     // status
     mpm::DevStatus* dstat = nullptr;
@@ -372,6 +372,6 @@ cudaError_t launch_step_done(mpm_ctx* c);
 
 // ---- adjoint (adjoint.cu)
 cudaError_t launch_adjoint(mpm_ctx* c, const float* adj_next, float* adj_cur, float4* gvbar, float4* gmbar,
-                           float4* gfbar, double* dE);
+                           float4* gfbar, double* dE, double* dphi);
 
 }  // namespace mpm

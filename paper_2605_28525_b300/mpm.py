@@ -102,7 +102,7 @@ def lib():
     L.mpm_state_bytes.restype = C.c_int64
     L.mpm_save_state.argtypes = [vp, vp]
     L.mpm_load_state.argtypes = [vp, vp]
-    L.mpm_adjoint_step.argtypes = [vp, vp, vp, C.POINTER(C.c_double)]
+    L.mpm_adjoint_step.argtypes = [vp, vp, vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.mpm_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
     L.mpm_set_tuning.argtypes = [vp, C.POINTER(Tuning)]
     L.mpm_create_ensemble.argtypes = [C.POINTER(Config), C.c_int32, C.POINTER(C.c_int64), vp, vp, vp, vp, vp,
@@ -313,13 +313,13 @@ class Simulation:
     def load_state(self, src):
         _check(lib().mpm_load_state(self.h, C.c_void_p(src.data_ptr())), self.h)
 
-    def adjoint_step(self, adj_next, adj_cur) -> float:
+    def adjoint_step(self, adj_next, adj_cur):
         """mpm_adjoint_step: adj_next, adj_cur are (n, 24) float32 CUDA tensors
-        (x, v, C, F adjoints in id order); returns this step's dL/dE."""
-        dE = C.c_double(0.0)
+        (x, v, C, F adjoints in id order); returns this step's (dL/dE, dL/dphi)."""
+        dE, dphi = C.c_double(0.0), C.c_double(0.0)
         _check(lib().mpm_adjoint_step(self.h, C.c_void_p(adj_next.data_ptr()), C.c_void_p(adj_cur.data_ptr()),
-                                      C.byref(dE)), self.h)
-        return dE.value
+                                      C.byref(dE), C.byref(dphi)), self.h)
+        return dE.value, dphi.value
 
     def stats(self):
         s = Stats()

@@ -1,7 +1,7 @@
-"""The hand-written adjoint of the explicit step (Neo-Hookean, deterministic
-mode) against FP64 central differences of the oracle: one step for every
-input family (x, v, C, F and Young's modulus E), and a checkpointed rollout
-through the torch.autograd.Function for E and the initial velocities."""
+"""The hand-written adjoint of the explicit step (deterministic mode) against
+FP64 central differences of the oracle: one step for every input family (x,
+v, C, F, Young's modulus E and, for Drucker-Prager, the friction angle phi),
+and checkpointed rollouts through the torch.autograd.Function."""
 import numpy as np
 import pytest
 
@@ -11,8 +11,12 @@ from tests.helpers import oracle_for, small_blob
 pytestmark = pytest.mark.gpu
 
 
-def _blob(floor=False):
-    wl, Cm, F = small_blob(n=2000, seed=21, E=1e5, vscale=0.5, cscale=2.0, fscale=0.03, dt=2e-4)
+def _blob(floor=False, dp=False):
+    wl, Cm, F = small_blob(n=2000, seed=21, E=1e5, vscale=0.5, cscale=2.0, fscale=0.03, dt=2e-4,
+                           material=W.DRUCKER_PRAGER if dp else W.NEOHOOKEAN)
+    if dp:
+        # per-particle friction angles (degrees)
+        wl.phi = np.random.default_rng(4).uniform(25.0, 35.0, wl.n).astype(np.float32)
     if floor:
         # a Coulomb floor under the blob's lower cells
         wl.floor_kind, wl.floor_z, wl.floor_mu = W.FLOOR_COULOMB, 12 * wl.dx, 0.3
@@ -38,30 +42,36 @@ def _pick(x, h, rng, k):
     return rng.choice(np.flatnonzero(ok), k, replace=False)
 
 
-@pytest.mark.parametrize("floor", [False, True])
-def test_one_step_adjoint_matches_fp64_differences(oracle_mod, floor):
+@pytest.mark.parametrize("floor,dp", [(False, False), (True, False), (False, True), (True, True)])
+def test_one_step_adjoint_matches_fp64_differences(oracle_mod, floor, dp):
     import torch
-    wl, Cm, F = _blob(floor)
+    wl, Cm, F = _blob(floor, dp)
     n = wl.n
     rng = np.random.default_rng(5)
     wts = (rng.standard_normal((n, 3)), rng.standard_normal((n, 3)), rng.standard_normal((n, 9)) * 1e-2,
            rng.standard_normal((n, 9)))
-    sim = mpm.Simulation(mpm.config_from_workload(wl, flags=mpm.DETERMINISTIC), wl.x, wl.v, Cm, F)
+    sim = mpm.Simulation(mpm.config_from_workload(wl, flags=mpm.DETERMINISTIC), wl.x, wl.v, Cm, F, phi=wl.phi)
     adj_next = torch.tensor(np.concatenate(wts, axis=1), dtype=torch.float32, device="cuda")
     adj_cur = torch.empty_like(adj_next)
-    dE = sim.adjoint_step(adj_next, adj_cur)
+    dE, dphi = sim.adjoint_step(adj_next, adj_cur)
     g = adj_cur.cpu().numpy().astype(np.float64)
 
     x0, v0, C0, F0 = (a.astype(np.float64) for a in (wl.x, wl.v, Cm, F))
+    phi0 = None if wl.phi is None else wl.phi.astype(np.float64)
     o = oracle_for(wl)
 
-    def L_of(x=x0, v=v0, C_=C0, F_=F0, orc=o):
-        return _L(orc.run(x, v, C_, F_, nsteps=1), wts)
+    def L_of(x=x0, v=v0, C_=C0, F_=F0, orc=o, phi=phi0):
+        return _L(orc.run(x, v, C_, F_, phi, nsteps=1), wts)
 
     # E
     dEr = 1e-5 * wl.E
     fd = (L_of(orc=_oracle(wl, wl.E + dEr)) - L_of(orc=_oracle(wl, wl.E - dEr))) / (2 * dEr)
+    assert fd != 0.0
     assert abs(dE - fd) <= 1e-3 * abs(fd), (dE, fd)
+    if dp:   # phi of every particle moved together
+        fdp = (L_of(phi=phi0 + 1e-4) - L_of(phi=phi0 - 1e-4)) / 2e-4
+        assert fdp != 0.0
+        assert abs(dphi - fdp) <= 1e-3 * abs(fdp), (dphi, fdp)
     # x, v, C, F of sampled particles
     ps = _pick(wl.x, wl.dx, rng, 6)
     fams = {"x": (x0, 0, 3, 1e-5 * wl.dx), "v": (v0, 3, 3, 1e-5), "C": (C0, 6, 9, 1e-4), "F": (F0, 15, 9, 1e-6)}
@@ -80,6 +90,7 @@ def test_one_step_adjoint_matches_fp64_differences(oracle_mod, floor):
                 want.append((L_of(**args1) - L_of(**args2)) / (2 * eps))
                 got.append(g[p, off + k])
         got, want = np.array(got), np.array(want)
+        assert np.abs(want).max() > 0
         assert np.abs(got - want).max() <= 1e-3 * np.abs(want).max(), (name, got, want)
 
 
@@ -133,11 +144,39 @@ def test_checkpointed_rollout_gradient(oracle_mod):
     assert np.abs(got - want).max() <= 1e-3 * np.abs(want).max(), (got, want)
 
 
+def test_dp_rollout_gradient_phi_and_E(oracle_mod):
+    """20 Drucker-Prager steps of a blob pressed onto a Coulomb floor,
+    checkpoints every 6: dL/dphi and dL/dE of its mean position (weighted
+    per axis) against FP64 differences."""
+    import torch
+    from paper_2605_28525_b300 import adjoint
+    wl, Cm, F = _blob(floor=True, dp=True)
+    n, K = wl.n, 20
+    c = np.tile(np.array([[0.2, 0.1, 1.0]]), (n, 1)) / n
+    sim = mpm.Simulation(mpm.config_from_workload(wl, flags=mpm.DETERMINISTIC), wl.x, wl.v, Cm, F, phi=wl.phi)
+    ckpts = adjoint.rollout(sim, K, 6)
+    adj = torch.zeros(n, 24, dtype=torch.float32, device="cuda")
+    adj[:, 0:3] = torch.tensor(c, dtype=torch.float32, device="cuda")
+    _, dE, dphi = adjoint.gradient(sim, ckpts, K, 6, adj)
+    x0, v0, C0, F0 = (a.astype(np.float64) for a in (wl.x, wl.v, Cm, F))
+    phi0 = wl.phi.astype(np.float64)
+
+    def L_of(E=wl.E, phi=phi0):
+        x, _, _, _ = _oracle(wl, E).run(x0, v0, C0, F0, phi, nsteps=K)
+        return float((x * c).sum())
+
+    fdp = (L_of(phi=phi0 + 1e-5) - L_of(phi=phi0 - 1e-5)) / 2e-5
+    fdE = (L_of(E=wl.E * (1 + 1e-6)) - L_of(E=wl.E * (1 - 1e-6))) / (2e-6 * wl.E)
+    assert fdp != 0.0 and fdE != 0.0
+    assert abs(dphi - fdp) <= 1e-3 * abs(fdp), (dphi, fdp)
+    assert abs(dE - fdE) <= 1e-3 * abs(fdE), (dE, fdE)
+
+
 def test_adjoint_refuses_unsupported_contexts(oracle_mod):
     import torch
     wl, Cm, F = _blob()
     adj = torch.zeros(wl.n, 24, device="cuda")
-    for flags, mat in [(0, W.NEOHOOKEAN), (mpm.DETERMINISTIC, W.DRUCKER_PRAGER)]:
+    for flags, mat in [(0, W.NEOHOOKEAN), (0, W.DRUCKER_PRAGER)]:
         wl.material = mat
         sim = mpm.Simulation(mpm.config_from_workload(wl, flags=flags), wl.x, wl.v, Cm, F)
         with pytest.raises(mpm.MpmError) as e:
