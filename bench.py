@@ -102,6 +102,8 @@ def make_workload(name: str):
         return W.elastic_cube()
     if name == "column_ensemble_64":
         return W.column_ensemble()
+    if name == "diff_column_262k":
+        return W.diff_column()
     raise SystemExit("unknown workload %s" % name)
 
 
@@ -330,6 +332,36 @@ def cpu_baseline(wl, nsteps):
     return wl.n * nsteps / dt, dt
 
 
+def adjoint_leg(wl, iters: int, every: int = 20):
+    """The differentiable column: the plain forward, one value-and-gradient
+    through the checkpointed adjoint, and an Adam calibration of phi from 30
+    deg towards a phi = 34 deg target run (deterministic mode throughout)."""
+    import torch
+    from paper_2605_28525_b300 import adjoint as A, mpm
+    target = A.column_target(wl, 34.0, wl.steps)
+    sim = mpm.Simulation(mpm.config_from_workload(wl, flags=mpm.DETERMINISTIC), wl.x, wl.v)
+    sim.step(1)
+    sim.close()
+    sim = mpm.Simulation(mpm.config_from_workload(wl, flags=mpm.DETERMINISTIC), wl.x, wl.v)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.step(wl.steps)
+    sim.read_particles()
+    t_fwd = time.perf_counter() - t0
+    sim.close()
+    t0 = time.perf_counter()
+    L, dphi, dE = A.column_value_and_grad(wl, wl.phi_deg, wl.E, target, wl.steps, every)
+    t_grad = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    hist = A.calibrate_phi(wl, target, wl.phi_deg, iters=iters, lr=0.5, every=every)
+    t_cal = time.perf_counter() - t0
+    return {"workload": wl.name, "particles": wl.n, "steps": wl.steps, "checkpoint_every": every,
+            "forward_s": t_fwd, "value_and_grad_s": t_grad, "cost_vs_forward": t_grad / t_fwd,
+            "loss": L, "dL_dphi_per_deg": dphi, "dL_dE": dE, "target_phi_deg": 34.0,
+            "calibration": {"iters": iters, "phi_deg": [hist[0][0], hist[-1][0]], "loss": [hist[0][1], hist[-1][1]],
+                            "seconds": t_cal}}
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -373,6 +405,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-flush", action="store_true")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="add the differentiable-column leg (diff_column_262k: gradients and calibration)")
+    ap.add_argument("--adjoint-iters", type=int, default=50)
     ap.add_argument("--compaction", default="hash", choices=["hash", "scan"],
                     help="active-set realisation: the hash (Sec. 4.3) or the scan (Sec. 4.2)")
     args = ap.parse_args()
@@ -450,6 +485,10 @@ def main():
                  "sparse_speedup": (wl.n / (total_ms / args.steps / 1e3)) / dense_value,
                  "occupancy_nodes": st["n_active_nodes"] / st["n_dense_nodes"]}
 
+    adj = None
+    if args.adjoint and rank == 0:
+        adj = adjoint_leg(W.diff_column() if wl.name != "diff_column_262k" else wl, args.adjoint_iters)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         from paper_2605_28525_b300 import workloads as W
@@ -478,6 +517,7 @@ def main():
             "e2e": e2e,
             "dense_gpu": dense,
             "gpu_launches": launches,
+            **({"adjoint": adj} if adj is not None else {}),
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)

@@ -64,12 +64,13 @@ def gradient(sim: "mpm.Simulation", ckpts, nsteps: int, every: int, adj_final: t
 
 
 class Rollout(torch.autograd.Function):
-    """(E, x0, v0) -> (x_n, v_n) through nsteps of a context built by
-    ``make_sim(E, x0, v0)``; checkpoints every ``every`` steps."""
+    """(E, phi, x0, v0) -> (x_n, v_n) through nsteps of a context built by
+    ``make_sim(E, phi, x0, v0)``; checkpoints every ``every`` steps.  E and
+    phi are 0-d tensors (phi in degrees, one angle for every particle)."""
 
     @staticmethod
-    def forward(ctx, E, x0, v0, make_sim, nsteps: int, every: int):
-        sim = make_sim(float(E), x0, v0)
+    def forward(ctx, E, phi, x0, v0, make_sim, nsteps: int, every: int):
+        sim = make_sim(float(E), float(phi), x0, v0)
         ckpts = rollout(sim, nsteps, every)
         out = sim.read_particles({"x": torch.empty_like(x0), "v": torch.empty_like(v0)})
         ctx.sim, ctx.ckpts, ctx.nsteps, ctx.every = sim, ckpts, nsteps, every
@@ -82,6 +83,79 @@ class Rollout(torch.autograd.Function):
         adj[:, 0:3] = gx
         if gv is not None:
             adj[:, 3:6] = gv
-        g0, dE, _ = gradient(ctx.sim, ctx.ckpts, ctx.nsteps, ctx.every, adj)
+        g0, dE, dphi = gradient(ctx.sim, ctx.ckpts, ctx.nsteps, ctx.every, adj)
         ctx.sim.close()
-        return (torch.tensor(dE, dtype=torch.float64), g0[:, 0:3].clone(), g0[:, 3:6].clone(), None, None, None)
+        f64 = torch.float64
+        return (torch.tensor(dE, dtype=f64), torch.tensor(dphi, dtype=f64), g0[:, 0:3].clone(), g0[:, 3:6].clone(),
+                None, None, None)
+
+
+# ------------------------------------------------------------ column collapse
+
+def runout(x: torch.Tensor, axis_xy, p: float = 8.0) -> torch.Tensor:
+    """Front runout: the p-norm mean of the particles' horizontal distance
+    from the column axis (a smooth stand-in for the largest distance)."""
+    d = x[:, :2].double() - torch.as_tensor(axis_xy, dtype=torch.float64, device=x.device)
+    r = torch.sqrt((d * d).sum(1) + 1e-12)
+    return (r ** p).mean() ** (1.0 / p)
+
+
+def column_loss(x: torch.Tensor, axis_xy, target) -> torch.Tensor:
+    """Squared error of the runout and of the particle-mean position against
+    a target (runout, mean) pair."""
+    R, m = runout(x, axis_xy), x.double().mean(0)
+    return (R - target[0]) ** 2 + ((m - target[1]) ** 2).sum()
+
+
+def column_target(wl, phi_target: float, nsteps: int):
+    """The (runout, mean position) of a forward run at phi_target."""
+    from . import mpm as M
+    sim = M.Simulation(M.config_from_workload(_with(wl, phi_deg=phi_target), flags=M.DETERMINISTIC), wl.x, wl.v)
+    sim.step(nsteps)
+    x = torch.tensor(sim.read_particles()["x"], device="cuda")
+    sim.close()
+    axis = _axis(wl)
+    return float(runout(x, axis)), x.double().mean(0)
+
+
+def _with(wl, **kw):
+    import dataclasses
+    return dataclasses.replace(wl, **kw)
+
+
+def _axis(wl):
+    return (float(wl.x[:, 0].mean()), float(wl.x[:, 1].mean()))
+
+
+def column_value_and_grad(wl, phi: float, E: float, target, nsteps: int, every: int):
+    """L(phi, E) of the column after nsteps and (dL/dphi, dL/dE)."""
+    from . import mpm as M
+    x0 = torch.tensor(wl.x, device="cuda")
+    v0 = torch.zeros_like(x0)
+
+    def make_sim(E_, phi_, x0_, v0_):
+        return M.Simulation(M.config_from_workload(_with(wl, E=E_, phi_deg=phi_), flags=M.DETERMINISTIC), x0_, v0_)
+
+    Et = torch.tensor(E, dtype=torch.float64, requires_grad=True)
+    pt = torch.tensor(phi, dtype=torch.float64, requires_grad=True)
+    xK, _ = Rollout.apply(Et, pt, x0, v0, make_sim, nsteps, every)
+    L = column_loss(xK, _axis(wl), target)
+    L.backward()
+    return float(L.detach()), float(pt.grad), float(Et.grad)
+
+
+def calibrate_phi(wl, target, phi0: float, iters: int = 50, lr: float = 0.5, every: int = 20):
+    """Adam on phi (degrees) against the target; returns the phi and loss
+    history."""
+    phi, m, v = phi0, 0.0, 0.0
+    b1, b2, eps = 0.9, 0.999, 1e-12
+    hist = []
+    for t in range(1, iters + 1):
+        L, g, _ = column_value_and_grad(wl, phi, wl.E, target, wl.steps, every)
+        hist.append((phi, L))
+        m = b1 * m + (1 - b1) * g
+        v = b2 * v + (1 - b2) * g * g
+        phi -= lr * (m / (1 - b1 ** t)) / (((v / (1 - b2 ** t)) ** 0.5) + eps)
+    L, _, _ = column_value_and_grad(wl, phi, wl.E, target, wl.steps, every)
+    hist.append((phi, L))
+    return hist

@@ -18,6 +18,11 @@ Workloads (paper Sec. 2.2 examples; exact sizes in the design notes):
                              [25, 35] deg.
   * ``sliding_block``     -- elastic block on a Coulomb floor with tilted gravity
                              (the paper's sliding-box benchmark, Sec. 2.2.1).
+  * ``diff_column``       -- the differentiable column: a 32^3-cell
+                             Drucker-Prager cube (262,144 particles, phi = 30
+                             deg, E = 5e6 Pa) in a 128x128x64 box at dx = 1/32,
+                             400 steps of 2e-4 s (dx coarser than the column
+                             collapse so that 400 steps see the collapse start).
   * ``column_ensemble``   -- independent granular columns, one per scenario,
                              each in its own 256x256x128 box at dx = 1/128:
                              particle counts log-uniform in [1e4, 5e5], phi
@@ -242,3 +247,13 @@ def ensemble_member(ens: Workload, s: int) -> Workload:
     return dataclasses.replace(ens, name="%s[%d]" % (ens.name, s), x=ens.x[a:b],
                                v=None if ens.v is None else ens.v[a:b],
                                phi=None if ens.phi is None else ens.phi[a:b], scenario_counts=None)
+
+
+def diff_column(cells: int = 32, seed: int = 6, steps: int = 400, phi_deg: float = 30.0, E: float = 5e6,
+                dx: float = 1.0 / 32.0, box=(128, 128, 64)) -> Workload:
+    """Drucker-Prager column of cells^3 cells at 8 particles per cell, centred
+    on a Coulomb floor (mu = 0.5 at z <= 3 dx) in a box of box nodes."""
+    c0x, c0y = box[0] // 2 - cells // 2, box[1] // 2 - cells // 2
+    x = jittered_cells((c0x, c0y, 3), (c0x + cells, c0y + cells, 3 + cells), dx, seed)
+    return Workload("diff_column_%dk" % (x.shape[0] // 1000), (0, 0, 0), tuple(box), dx, 2e-4, (0.0, 0.0, -9.81),
+                    DRUCKER_PRAGER, E, 0.3, 2000.0, phi_deg, 8.0, FLOOR_COULOMB, 3 * dx, 0.5, x, steps=steps)

@@ -104,7 +104,7 @@ def test_checkpointed_rollout_gradient(oracle_mod):
     C_d = torch.tensor(Cm, device="cuda")
     F_d = torch.tensor(F, device="cuda")
 
-    def make_sim(E, x0, v0):
+    def make_sim(E, phi, x0, v0):
         import dataclasses
         cfg = mpm.config_from_workload(dataclasses.replace(wl, E=E), flags=mpm.DETERMINISTIC)
         return mpm.Simulation(cfg, x0, v0, C_d, F_d)
@@ -112,9 +112,10 @@ def test_checkpointed_rollout_gradient(oracle_mod):
     grads = []
     for every in (7, K):
         E = torch.tensor(wl.E, dtype=torch.float64, requires_grad=True)
+        phi = torch.tensor(30.0, dtype=torch.float64)
         x0 = torch.tensor(wl.x, device="cuda", requires_grad=True)
         v0 = torch.tensor(wl.v, device="cuda", requires_grad=True)
-        xK, vK = adjoint.Rollout.apply(E, x0, v0, make_sim, K, every)
+        xK, vK = adjoint.Rollout.apply(E, phi, x0, v0, make_sim, K, every)
         loss = (xK.double() * torch.tensor(cx, device="cuda")).sum() + \
                (vK.double() * torch.tensor(cv, device="cuda")).sum()
         loss.backward()
@@ -182,3 +183,48 @@ def test_adjoint_refuses_unsupported_contexts(oracle_mod):
         with pytest.raises(mpm.MpmError) as e:
             sim.adjoint_step(adj, torch.empty_like(adj))
         assert e.value.status == mpm.ERR_INVALID_ARG
+
+
+def test_column_functional_gradient_matches_fp64(oracle_mod):
+    """The differentiable column's geometry (an 8^3-cell cube), squeezed by
+    an initial velocity field towards its centre so that 50 steps see both
+    the elastic and the plastic response, without a floor (a body at rest
+    on a Coulomb floor keeps nodes on the kinks of the friction law, where
+    central differences of a 50-step trajectory are not smooth; the floor's
+    adjoint is checked step by step above): the gradient of the front runout
+    plus a weighted mean position with respect to phi and E, through the
+    checkpointed autograd.Function, against FP64 central differences of the
+    same functional on the oracle's trajectories."""
+    import dataclasses
+    import torch
+    from paper_2605_28525_b300 import adjoint
+    wl = W.diff_column(cells=8, steps=50, box=(32, 32, 24))
+    wl = dataclasses.replace(wl, floor_kind=W.FLOOR_NONE, gravity=(0.0, 0.0, 0.0))
+    c = wl.x.astype(np.float64).mean(0)
+    v0n = (-4.0 * (wl.x - c) * np.array([1.0, 1.0, 0.5])).astype(np.float32)
+    axis = adjoint._axis(wl)
+    wts = torch.tensor([0.3, 0.2, 1.0], dtype=torch.float64)
+
+    def J(x):
+        return adjoint.runout(x, axis) + (x.double().mean(0) * wts.to(x.device)).sum()
+
+    def make_sim(E_, phi_, x0_, v0_):
+        return mpm.Simulation(mpm.config_from_workload(dataclasses.replace(wl, E=E_, phi_deg=phi_),
+                                                       flags=mpm.DETERMINISTIC), x0_, v0_)
+
+    Et = torch.tensor(wl.E, dtype=torch.float64, requires_grad=True)
+    pt = torch.tensor(30.0, dtype=torch.float64, requires_grad=True)
+    x0 = torch.tensor(wl.x, device="cuda")
+    xK, _ = adjoint.Rollout.apply(Et, pt, x0, torch.tensor(v0n, device="cuda"), make_sim, wl.steps, 16)
+    J(xK).backward()
+
+    def J_of(phi=30.0, E=wl.E):
+        o = oracle_for(dataclasses.replace(wl, E=E, phi_deg=phi))
+        x, _, _, _ = o.run(wl.x.astype(np.float64), v0n.astype(np.float64), nsteps=wl.steps)
+        return float(J(torch.tensor(x)))
+
+    fdp = (J_of(phi=30.0 + 1e-5) - J_of(phi=30.0 - 1e-5)) / 2e-5
+    fdE = (J_of(E=wl.E * (1 + 1e-6)) - J_of(E=wl.E * (1 - 1e-6))) / (2e-6 * wl.E)
+    assert fdp != 0.0 and fdE != 0.0
+    assert abs(float(pt.grad) - fdp) <= 1e-3 * abs(fdp), (float(pt.grad), fdp)
+    assert abs(float(Et.grad) - fdE) <= 1e-3 * abs(fdE), (float(Et.grad), fdE)
