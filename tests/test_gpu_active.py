@@ -137,3 +137,42 @@ def test_phase_order_is_enforced(oracle_mod):
     sim.p2g()
     sim.grid_update()
     sim.g2p()
+
+
+@pytest.mark.parametrize("B", [1, 4])
+@pytest.mark.parametrize("flags", [0, mpm.SCAN_COMPACTION])
+def test_negative_coordinates_and_box_edges(oracle_mod, B, flags):
+    """A box with negative node indices (Eq. (key)'s bias b in use) and
+    particles whose stencils touch the first and the last node of the box on
+    every axis: bit-exact active set, then P2G against the oracle."""
+    dx = 1.0 / 16
+    lo, hi = (-40, -9, -23), (7, 30, 2)
+    rng = np.random.default_rng(17)
+    n = 3000
+    x = np.empty((n, 3), np.float32)
+    for a in range(3):
+        # stencil base in [lo, hi - 2]: x/h in [lo + 0.5, hi - 0.5)
+        x[:, a] = ((lo[a] + 0.5) + rng.random(n) * (hi[a] - lo[a] - 1.0 - 1e-3)) * dx
+    # extremes on every axis
+    for a in range(3):
+        x[a, a] = np.float32((lo[a] + 0.5) * dx)
+        x[3 + a, a] = np.float32((hi[a] - 0.5 - 1e-3) * dx)
+    wl = W.Workload("edges", lo, hi, dx, 1e-4, (0.0, 0.0, -9.81), W.NEOHOOKEAN, 1e4, 0.3, 1000.0, 30.0, 8.0,
+                    W.FLOOR_NONE, 0.0, 0.0, x, block_size=B, wall_layers=0)
+    sim = mpm.Simulation(mpm.config_from_workload(wl, flags=flags), x)
+    keys = _gpu_keys(sim)
+    o = oracle_for(wl)
+    assert np.array_equal(keys, eq_keys(o.active_blocks(x)))
+    b = mpm.unpack_keys(keys)
+    assert b.min(0).tolist() == [lo[a] // B for a in range(3)]
+    assert b.max(0).tolist() == [hi[a] // B for a in range(3)]
+    sim.p2g()
+    g = sim.read_grid()
+    m, mv, f = o.p2g(x)
+    from tests.helpers import sparse_node_coords
+    nodes = sparse_node_coords(keys, B)
+    ok = np.all((nodes >= np.array(lo)) & (nodes <= np.array(hi)), axis=1)   # blocks overhang the box
+    idx = o.node_index(nodes[ok])
+    assert np.abs(g["m"][ok] - m[idx]).max() <= 1e-6 * np.abs(m).max()
+    assert np.abs(g["mv"][ok] - mv[idx]).max() <= 1e-6 * np.abs(mv).max()
+    assert np.all(g["m"][~ok] == 0)
