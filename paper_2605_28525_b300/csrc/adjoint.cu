@@ -163,7 +163,9 @@ __device__ bool dsvd3(const float Ff[9], double U[3][3], double sg[3], double V[
             S[i][j] = F[i] * F[j] + F[3 + i] * F[3 + j] + F[6 + i] * F[6 + j];
             V[i][j] = i == j ? 1.0 : 0.0;
         }
-    for (int sweep = 0; sweep < 12; ++sweep) {
+    for (int sweep = 0; sweep < 10; ++sweep) {   // quadratic convergence: a few sweeps reach FP64 rounding
+        const double off = fabs(S[0][1]) + fabs(S[0][2]) + fabs(S[1][2]);
+        if (off <= 1e-16 * (fabs(S[0][0]) + fabs(S[1][1]) + fabs(S[2][2]))) break;
         djacobi(S, V, 0, 1);
         djacobi(S, V, 0, 2);
         djacobi(S, V, 1, 2);
