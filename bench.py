@@ -362,6 +362,32 @@ def adjoint_leg(wl, iters: int, every: int = 20):
                             "seconds": t_cal}}
 
 
+def occupancy_sweep(boxes=(128, 256, 512, 1024), steps: int = 20):
+    """The 1M column in boxes of growing width (same body): sparse and dense
+    GPU steps against the node occupancy, as the paper's sparse-vs-dense
+    figure does for its examples."""
+    import torch
+    from paper_2605_28525_b300 import mpm, workloads as W
+    out = []
+    for b in boxes:
+        wl = W.column_collapse(box_xy=b)
+        row = {"box": "%dx%dx256" % (b, b)}
+        for name, flags in (("sparse", 0), ("dense", mpm.DENSE_GRID)):
+            sim = mpm.Simulation.from_workload(wl, flags=flags, stream=torch.cuda.current_stream(), device_inputs=True)
+            for _ in range(3):
+                sim.step(1)
+            ms = float(np.mean(time_steps(sim, steps, None)))
+            st = sim.stats()
+            sim.close()
+            row[name + "_ms"] = ms
+            if name == "sparse":
+                row["occupancy_nodes"] = st["n_active_nodes"] / st["n_dense_nodes"]
+        row["speedup"] = row["dense_ms"] / row["sparse_ms"]
+        out.append(row)
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -408,6 +434,8 @@ def main():
     ap.add_argument("--adjoint", action="store_true",
                     help="add the differentiable-column leg (diff_column_262k: gradients and calibration)")
     ap.add_argument("--adjoint-iters", type=int, default=50)
+    ap.add_argument("--sweep", action="store_true",
+                    help="add the sparse-vs-dense occupancy sweep of the 1M column (boxes 128..1024 wide)")
     ap.add_argument("--compaction", default="hash", choices=["hash", "scan"],
                     help="active-set realisation: the hash (Sec. 4.3) or the scan (Sec. 4.2)")
     args = ap.parse_args()
@@ -485,6 +513,7 @@ def main():
                  "sparse_speedup": (wl.n / (total_ms / args.steps / 1e3)) / dense_value,
                  "occupancy_nodes": st["n_active_nodes"] / st["n_dense_nodes"]}
 
+    sweep = occupancy_sweep() if (args.sweep and rank == 0) else None
     adj = None
     if args.adjoint and rank == 0:
         adj = adjoint_leg(W.diff_column() if wl.name != "diff_column_262k" else wl, args.adjoint_iters)
@@ -518,6 +547,7 @@ def main():
             "dense_gpu": dense,
             "gpu_launches": launches,
             **({"adjoint": adj} if adj is not None else {}),
+            **({"occupancy_sweep": sweep} if sweep is not None else {}),
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)

@@ -115,14 +115,17 @@ def elastic_cube(seed: int = 0, steps: int = 200) -> Workload:
 
 
 def column_collapse(cells_xy: int = 32, cells_z: int = 128, seed: int = 0, steps: int = 2000,
-                    phi_deg: float = 30.0) -> Workload:
-    """512x512x256 box at dx = 1/128; DP column centred at (2, 2) m on a Coulomb floor at z = 3 dx."""
+                    phi_deg: float = 30.0, box_xy: int = 512) -> Workload:
+    """box_xy x box_xy x 256 box (512 by default) at dx = 1/128; DP column
+    centred in x and y (at (2, 2) m by default) on a Coulomb floor at z = 3 dx.
+    The particles do not depend on box_xy other than by the shift that keeps
+    the column centred."""
     dx = 1.0 / 128.0
-    c0 = 256 - cells_xy // 2
+    c0 = box_xy // 2 - cells_xy // 2
     x = jittered_cells((c0, c0, 3), (c0 + cells_xy, c0 + cells_xy, 3 + cells_z), dx, seed)
     n = x.shape[0]
     return Workload("column_collapse_%dk" % (n // 1024) if n < 1 << 20 else "column_collapse_%dM" % (n >> 20),
-                    (0, 0, 0), (512, 512, 256), dx, 2e-5, (0.0, 0.0, -9.81),
+                    (0, 0, 0), (box_xy, box_xy, 256), dx, 2e-5, (0.0, 0.0, -9.81),
                     DRUCKER_PRAGER, 1e7, 0.3, 2000.0, phi_deg, 8.0, FLOOR_COULOMB, 3 * dx, 0.5, x,
                     steps=steps)
 
