@@ -39,7 +39,7 @@ def _newer(src_list, target):
 
 
 def build(force: bool = False, verbose: bool = False, out: str = LIB, obj_dir: str = OBJ, defines=()) -> str:
-    """Compile every csrc/*.cu and link `out`.  `defines` (e.g. ("MPM_SVD_SWEEPS=4",))
+    """Compile every csrc/*.cu and link `out`.  `defines` (e.g. ("MPM_JACOBI_SWEEPS=3",))
     and a separate `obj_dir` build variants side by side."""
     os.makedirs(obj_dir, exist_ok=True)
     extra = ["-D" + d for d in defines]

@@ -1047,7 +1047,7 @@ mpm_status mpm_autotune(mpm_ctx* c, int32_t repeats, mpm_tuning* out) {
     CK(launch_grid_update(c));
     // G2P reads the current buffer and writes the other one: reruns repeat it
     for (int threads = 128; threads <= 256; threads *= 2)
-        for (int mb = 2; mb <= 3; ++mb) {
+        for (int mb = 2; mb <= 4; ++mb) {
             c->tune.g2p_threads = threads;
             c->tune.g2p_min_blocks = mb;
             double ms = 0;
@@ -1082,9 +1082,9 @@ mpm_status mpm_get_tuning(mpm_ctx* c, mpm_tuning* out) {
 mpm_status mpm_set_tuning(mpm_ctx* c, const mpm_tuning* in) {
     if (!c || !in) return MPM_ERR_INVALID_ARG;
     if (in->p2g_ctas_per_sm < 1 || in->p2g_ctas_per_sm > 8 || (in->g2p_threads != 128 && in->g2p_threads != 256) ||
-        (in->g2p_min_blocks != 2 && in->g2p_min_blocks != 3))
+        in->g2p_min_blocks < 2 || in->g2p_min_blocks > 4)
         return fail(c, MPM_ERR_INVALID_ARG, "tuning outside p2g_ctas_per_sm 1..8, g2p_threads 128/256, "
-                                            "g2p_min_blocks 2/3");
+                                            "g2p_min_blocks 2..4");
     c->tune.p2g_ctas_per_sm = in->p2g_ctas_per_sm;
     c->tune.g2p_threads = in->g2p_threads;
     c->tune.g2p_min_blocks = in->g2p_min_blocks;

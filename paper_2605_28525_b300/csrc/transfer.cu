@@ -490,8 +490,8 @@ __device__ __forceinline__ bool nh_tau(const Params& P, const float F[9], Sym& t
     return true;
 }
 
-#ifndef MPM_SVD_SWEEPS
-#define MPM_SVD_SWEEPS 4
+#ifndef MPM_JACOBI_SWEEPS
+#define MPM_JACOBI_SWEEPS 4   // at most
 #endif
 
 // One Jacobi rotation of the symmetric S in the (p, q) plane, accumulated in
@@ -525,132 +525,227 @@ __device__ __forceinline__ void jacobi_rot(float S[3][3], float V[3][3]) {
     }
 }
 
-// SVD F = U diag(sig) V^T in FP32 (McAdams et al. 2011 structure: Jacobi
-// eigenanalysis of F^T F for V, then an orthogonalisation of F V for U).
-// sig is descending with sig[2] carrying the sign of det F.
-__device__ __forceinline__ bool svd3(const float F[9], float U[3][3], float sig[3], float V[3][3]) {
+#ifndef MPM_JACOBI_TOL
+#define MPM_JACOBI_TOL 1e-7f
+#endif
+
+// Jacobi eigenanalysis of the symmetric S: on return its diagonal holds the
+// eigenvalues (unordered) and the columns of U the eigenvectors.  From the
+// third sweep on, a thread whose off-diagonal entries are all below
+// MPM_JACOBI_TOL of the trace stops; the test is per thread, so a particle's
+// result does not depend on the other particles of its warp.
+__device__ __forceinline__ void jacobi_eig3(float S[3][3], float U[3][3]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) U[i][j] = (i == j) ? 1.f : 0.f;
+#pragma unroll
+    for (int sweep = 0; sweep < MPM_JACOBI_SWEEPS; ++sweep) {
+        if (sweep >= 2) {
+            const float tol = MPM_JACOBI_TOL * (fabsf(S[0][0]) + fabsf(S[1][1]) + fabsf(S[2][2]));
+            if (fabsf(S[0][1]) <= tol && fabsf(S[0][2]) <= tol && fabsf(S[1][2]) <= tol) break;
+        }
+        jacobi_rot<0, 1, 2>(S, U);
+        jacobi_rot<0, 2, 1>(S, U);
+        jacobi_rot<1, 2, 0>(S, U);
+    }
+}
+
+// Principal Hencky strains of F from the left Cauchy-Green tensor
+// b = F F^T = U diag(exp(2 eps)) U^T.  False when det F <= 0 or b is not
+// positive definite in FP32.
+__device__ __forceinline__ bool left_hencky(const float F[9], float U[3][3], float eps[3]) {
+    if (!(det3(F) > 0.f)) return false;
     float S[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            S[i][j] = F[0 * 3 + i] * F[0 * 3 + j] + F[1 * 3 + i] * F[1 * 3 + j] + F[2 * 3 + i] * F[2 * 3 + j];
-            V[i][j] = (i == j) ? 1.f : 0.f;
-        }
-#pragma unroll
-    for (int sweep = 0; sweep < MPM_SVD_SWEEPS; ++sweep) {
-        jacobi_rot<0, 1, 2>(S, V);
-        jacobi_rot<0, 2, 1>(S, V);
-        jacobi_rot<1, 2, 0>(S, V);
-    }
-    float ev[3] = {S[0][0], S[1][1], S[2][2]};
-    // sort eigenvalues (and columns of V) descending
-#define MPM_SWAPCOL(a, b)                              \
-    {                                                  \
-        float te = ev[a];                              \
-        ev[a] = ev[b];                                 \
-        ev[b] = te;                                    \
-        for (int k = 0; k < 3; ++k) {                  \
-            float tv = V[k][a];                        \
-            V[k][a] = V[k][b];                         \
-            V[k][b] = tv;                              \
-        }                                              \
-    }
-    if (ev[0] < ev[1]) MPM_SWAPCOL(0, 1);
-    if (ev[0] < ev[2]) MPM_SWAPCOL(0, 2);
-    if (ev[1] < ev[2]) MPM_SWAPCOL(1, 2);
-#undef MPM_SWAPCOL
-    // make V a rotation
-    const float dv = V[0][0] * (V[1][1] * V[2][2] - V[1][2] * V[2][1]) - V[0][1] * (V[1][0] * V[2][2] - V[1][2] * V[2][0]) +
-                     V[0][2] * (V[1][0] * V[2][1] - V[1][1] * V[2][0]);
-    if (dv < 0.f) {
-        V[0][2] = -V[0][2];
-        V[1][2] = -V[1][2];
-        V[2][2] = -V[2][2];
-    }
-    float Bc[3][3];   // B = F V, columns b_j
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) Bc[i][j] = F[i * 3 + 0] * V[0][j] + F[i * 3 + 1] * V[1][j] + F[i * 3 + 2] * V[2][j];
-    const float n0 = sqrtf(Bc[0][0] * Bc[0][0] + Bc[1][0] * Bc[1][0] + Bc[2][0] * Bc[2][0]);
-    if (!(n0 > 0.f)) return false;
-    float u0[3] = {Bc[0][0] / n0, Bc[1][0] / n0, Bc[2][0] / n0};
-    const float d01 = u0[0] * Bc[0][1] + u0[1] * Bc[1][1] + u0[2] * Bc[2][1];
-    float u1[3] = {Bc[0][1] - d01 * u0[0], Bc[1][1] - d01 * u0[1], Bc[2][1] - d01 * u0[2]};
-    const float n1 = sqrtf(u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
-    if (!(n1 > 0.f)) return false;
-    u1[0] /= n1;
-    u1[1] /= n1;
-    u1[2] /= n1;
-    const float u2[3] = {u0[1] * u1[2] - u0[2] * u1[1], u0[2] * u1[0] - u0[0] * u1[2], u0[0] * u1[1] - u0[1] * u1[0]};
-    sig[0] = n0;
-    sig[1] = n1;
-    sig[2] = u2[0] * Bc[0][2] + u2[1] * Bc[1][2] + u2[2] * Bc[2][2];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        U[i][0] = u0[i];
-        U[i][1] = u1[i];
-        U[i][2] = u2[i];
-    }
+        for (int j = i; j < 3; ++j)
+            S[i][j] = S[j][i] = F[i * 3 + 0] * F[j * 3 + 0] + F[i * 3 + 1] * F[j * 3 + 1] + F[i * 3 + 2] * F[j * 3 + 2];
+    jacobi_eig3(S, U);
+    if (!(S[0][0] > 0.f && S[1][1] > 0.f && S[2][2] > 0.f)) return false;
+    eps[0] = 0.5f * logf(S[0][0]);
+    eps[1] = 0.5f * logf(S[1][1]);
+    eps[2] = 0.5f * logf(S[2][2]);
     return true;
 }
 
+// tau = U diag(2 mu H + lambda tr H) U^T, the Hencky Kirchhoff stress.
+__device__ __forceinline__ void hencky_stress(const Params& P, const float U[3][3], const float H[3], Sym& t) {
+    const float trH = H[0] + H[1] + H[2];
+    const float d[3] = {2.f * P.mu * H[0] + P.lambda * trH, 2.f * P.mu * H[1] + P.lambda * trH,
+                        2.f * P.mu * H[2] + P.lambda * trH};
+    t.xx = U[0][0] * U[0][0] * d[0] + U[0][1] * U[0][1] * d[1] + U[0][2] * U[0][2] * d[2];
+    t.yy = U[1][0] * U[1][0] * d[0] + U[1][1] * U[1][1] * d[1] + U[1][2] * U[1][2] * d[2];
+    t.zz = U[2][0] * U[2][0] * d[0] + U[2][1] * U[2][1] * d[1] + U[2][2] * U[2][2] * d[2];
+    t.xy = U[0][0] * U[1][0] * d[0] + U[0][1] * U[1][1] * d[1] + U[0][2] * U[1][2] * d[2];
+    t.xz = U[0][0] * U[2][0] * d[0] + U[0][1] * U[2][1] * d[1] + U[0][2] * U[2][2] * d[2];
+    t.yz = U[1][0] * U[2][0] * d[0] + U[1][1] * U[2][1] * d[1] + U[1][2] * U[2][2] * d[2];
+}
+
 // Drucker-Prager return map in principal Hencky strain (Klar et al. 2016) on
-// the elastic trial F; writes the projected F and the Hencky Kirchhoff stress.
-__device__ __forceinline__ bool dp_update(const Params& P, float alpha, float F[9], Sym& t) {
-    float U[3][3], sig[3], V[3][3];
-    if (!svd3(F, U, sig, V)) return false;
-    if (!(sig[2] > 0.f)) return false;
-    float eps[3] = {logf(sig[0]), logf(sig[1]), logf(sig[2])};
+// the elastic trial F, through the left stretch: with F = U diag(e^eps) V^T,
+// the projected F is U diag(e^H) V^T = U diag(e^(H - eps)) U^T F, so V is
+// never formed and a state inside the cone keeps its F unchanged.  Writes the
+// projected F and the Hencky Kirchhoff stress.
+__device__ __forceinline__ bool dp_update_eig(const Params& P, float alpha, float F[9], Sym& t) {
+    float U[3][3], eps[3];
+    if (!left_hencky(F, U, eps)) return false;
     const float tr = eps[0] + eps[1] + eps[2];
     const float dev[3] = {eps[0] - tr * (1.f / 3.f), eps[1] - tr * (1.f / 3.f), eps[2] - tr * (1.f / 3.f)};
     const float nd = sqrtf(dev[0] * dev[0] + dev[1] * dev[1] + dev[2] * dev[2]);
     const float dgamma = nd + (3.f * P.lambda + 2.f * P.mu) / (2.f * P.mu) * tr * alpha;
     float H[3];
-    if (tr >= 0.f) {
-        H[0] = H[1] = H[2] = 0.f;                   // tip of the cone
-    } else if (dgamma <= 0.f) {
-        H[0] = eps[0];                               // inside the cone
+    if (tr < 0.f && dgamma <= 0.f) {
+        H[0] = eps[0];                               // inside the cone: F unchanged
         H[1] = eps[1];
         H[2] = eps[2];
     } else {
-        const float k = dgamma / nd;                 // onto the cone, volume kept
-        H[0] = eps[0] - k * dev[0];
-        H[1] = eps[1] - k * dev[1];
-        H[2] = eps[2] - k * dev[2];
+        if (tr >= 0.f) {
+            H[0] = H[1] = H[2] = 0.f;                // tip of the cone
+        } else {
+            const float k = dgamma / nd;             // onto the cone, volume kept
+            H[0] = eps[0] - k * dev[0];
+            H[1] = eps[1] - k * dev[1];
+            H[2] = eps[2] - k * dev[2];
+        }
+        const float s[3] = {expf(H[0] - eps[0]), expf(H[1] - eps[1]), expf(H[2] - eps[2])};
+        float M[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = i; j < 3; ++j)
+                M[i][j] = M[j][i] = U[i][0] * s[0] * U[j][0] + U[i][1] * s[1] * U[j][1] + U[i][2] * s[2] * U[j][2];
+        float G[9];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) G[i * 3 + j] = M[i][0] * F[0 * 3 + j] + M[i][1] * F[1 * 3 + j] + M[i][2] * F[2 * 3 + j];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) F[k] = G[k];
     }
-    const float e[3] = {expf(H[0]), expf(H[1]), expf(H[2])};
+    hencky_stress(P, U, H, t);
+    return true;
+}
+
+// ---- the same return map without an eigenanalysis, for a stretch near I
+//
+// All the map needs are isotropic matrix functions of b = F F^T: the Hencky
+// strain eps = ln(b) / 2, and, since H and eps share their eigenvectors, the
+// projected F = exp(H) exp(-eps) F = exp(H - eps) F with H - eps = -k dev eps
+// on the cone and -eps at its tip.  When X = b - I is small, ln(I + X) and
+// exp come from their power series, with products of symmetric matrices that
+// commute (polynomials in X); larger stretches take the Jacobi path above.
+
+#ifndef MPM_SERIES_MAX
+#define MPM_SERIES_MAX 0.0625f   // ||F F^T - I||_F up to which the series path is taken
+#endif
+
+// A B for symmetric A and B that commute: the product is symmetric.
+__device__ __forceinline__ Sym sym_mul(const Sym& a, const Sym& b) {
+    Sym r;
+    r.xx = a.xx * b.xx + a.xy * b.xy + a.xz * b.xz;
+    r.xy = a.xx * b.xy + a.xy * b.yy + a.xz * b.yz;
+    r.xz = a.xx * b.xz + a.xy * b.yz + a.xz * b.zz;
+    r.yy = a.xy * b.xy + a.yy * b.yy + a.yz * b.yz;
+    r.yz = a.xy * b.xz + a.yy * b.yz + a.yz * b.zz;
+    r.zz = a.xz * b.xz + a.yz * b.yz + a.zz * b.zz;
+    return r;
+}
+
+__device__ __forceinline__ Sym sym_axpi(const Sym& a, float s, float d) {   // s A + d I
+    return Sym{s * a.xx + d, s * a.xy, s * a.xz, s * a.yy + d, s * a.yz, s * a.zz + d};
+}
+
+__device__ __forceinline__ float sym_norm2(const Sym& a) {   // squared Frobenius norm
+    return a.xx * a.xx + a.yy * a.yy + a.zz * a.zz + 2.f * (a.xy * a.xy + a.xz * a.xz + a.yz * a.yz);
+}
+
+// X = F F^T - I.  The diagonal is formed as (F_ii - 1)(F_ii + 1) + the other
+// two squares, so the cancellation against 1 happens exactly.
+__device__ __forceinline__ Sym left_cg_minus_i(const float F[9]) {
+    Sym X;
+    X.xx = fmaf(F[0] - 1.f, F[0] + 1.f, F[1] * F[1] + F[2] * F[2]);
+    X.yy = fmaf(F[4] - 1.f, F[4] + 1.f, F[3] * F[3] + F[5] * F[5]);
+    X.zz = fmaf(F[8] - 1.f, F[8] + 1.f, F[6] * F[6] + F[7] * F[7]);
+    X.xy = F[0] * F[3] + F[1] * F[4] + F[2] * F[5];
+    X.xz = F[0] * F[6] + F[1] * F[7] + F[2] * F[8];
+    X.yz = F[3] * F[6] + F[4] * F[7] + F[5] * F[8];
+    return X;
+}
+
+// eps = ln(I + X) / 2 from X - X^2/2 + X^3/3 - X^4/4 + X^5/5 (Horner).  At
+// ||X||_F <= 1/16 the first omitted term is below 2e-8 in eps.
+__device__ __forceinline__ Sym hencky_series(const Sym& X) {
+    Sym q = sym_axpi(X, 0.2f, -0.25f);
+    q = sym_axpi(sym_mul(q, X), 1.f, 1.f / 3.f);
+    q = sym_axpi(sym_mul(q, X), 1.f, -0.5f);
+    q = sym_axpi(sym_mul(q, X), 1.f, 1.f);
+    return sym_axpi(sym_mul(q, X), 0.5f, 0.f);
+}
+
+// exp(Y) = I + Y + Y^2/2 + Y^3/6 + Y^4/24 (Horner), for ||Y||_F <= 1/32 here,
+// where the first omitted term is below 3e-10.
+__device__ __forceinline__ Sym exp_series(const Sym& Y) {
+    Sym e = sym_axpi(Y, 0.25f, 1.f);
+    e = sym_axpi(sym_mul(Y, e), 1.f / 3.f, 1.f);
+    e = sym_axpi(sym_mul(Y, e), 0.5f, 1.f);
+    return sym_axpi(sym_mul(Y, e), 1.f, 1.f);
+}
+
+__device__ __forceinline__ void hencky_stress_sym(const Params& P, const Sym& H, Sym& t) {
+    const float l = P.lambda * (H.xx + H.yy + H.zz), m2 = 2.f * P.mu;
+    t = Sym{m2 * H.xx + l, m2 * H.xy, m2 * H.xz, m2 * H.yy + l, m2 * H.yz, m2 * H.zz + l};
+}
+
+// Drucker-Prager return map (the reading above): the series form when
+// ||F F^T - I||_F <= MPM_SERIES_MAX, else the eigenanalysis.
+__device__ __forceinline__ bool dp_update(const Params& P, float alpha, float F[9], Sym& t) {
+    const Sym X = left_cg_minus_i(F);
+    if (!(sym_norm2(X) <= MPM_SERIES_MAX * MPM_SERIES_MAX)) return dp_update_eig(P, alpha, F, t);
+    if (!(det3(F) > 0.f)) return false;
+    const Sym e = hencky_series(X);
+    const float tr = e.xx + e.yy + e.zz;
+    const Sym dev = sym_axpi(e, 1.f, -tr * (1.f / 3.f));
+    const float nd = sqrtf(sym_norm2(dev));
+    const float dgamma = nd + (3.f * P.lambda + 2.f * P.mu) / (2.f * P.mu) * tr * alpha;
+    Sym H = e;                                       // inside the cone: F unchanged
+    if (!(tr < 0.f && dgamma <= 0.f)) {
+        Sym Y;                                       // H - eps
+        if (tr >= 0.f) {
+            Y = sym_axpi(e, -1.f, 0.f);              // tip of the cone: H = 0
+            H = Sym{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        } else {
+            const float k = dgamma / nd;             // onto the cone, volume kept
+            Y = sym_axpi(dev, -k, 0.f);
+            H = Sym{e.xx + Y.xx, e.xy + Y.xy, e.xz + Y.xz, e.yy + Y.yy, e.yz + Y.yz, e.zz + Y.zz};
+        }
+        const Sym E = exp_series(Y);
+        const float M[9] = {E.xx, E.xy, E.xz, E.xy, E.yy, E.yz, E.xz, E.yz, E.zz};
+        float G[9];
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+        for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) F[i * 3 + j] = U[i][0] * e[0] * V[j][0] + U[i][1] * e[1] * V[j][1] + U[i][2] * e[2] * V[j][2];
-    const float trH = H[0] + H[1] + H[2];
-    const float d[3] = {2.f * P.mu * H[0] + P.lambda * trH, 2.f * P.mu * H[1] + P.lambda * trH,
-                        2.f * P.mu * H[2] + P.lambda * trH};
-    t.xx = U[0][0] * U[0][0] * d[0] + U[0][1] * U[0][1] * d[1] + U[0][2] * U[0][2] * d[2];
-    t.yy = U[1][0] * U[1][0] * d[0] + U[1][1] * U[1][1] * d[1] + U[1][2] * U[1][2] * d[2];
-    t.zz = U[2][0] * U[2][0] * d[0] + U[2][1] * U[2][1] * d[1] + U[2][2] * U[2][2] * d[2];
-    t.xy = U[0][0] * U[1][0] * d[0] + U[0][1] * U[1][1] * d[1] + U[0][2] * U[1][2] * d[2];
-    t.xz = U[0][0] * U[2][0] * d[0] + U[0][1] * U[2][1] * d[1] + U[0][2] * U[2][2] * d[2];
-    t.yz = U[1][0] * U[2][0] * d[0] + U[1][1] * U[2][1] * d[1] + U[1][2] * U[2][2] * d[2];
+            for (int j = 0; j < 3; ++j)
+                G[i * 3 + j] = M[i * 3 + 0] * F[0 * 3 + j] + M[i * 3 + 1] * F[1 * 3 + j] + M[i * 3 + 2] * F[2 * 3 + j];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) F[k] = G[k];
+    }
+    hencky_stress_sym(P, H, t);
     return true;
 }
 
 // Hencky stress of an F without plastic projection (initial state).
 __device__ __forceinline__ bool hencky_tau(const Params& P, const float F[9], Sym& t) {
-    float U[3][3], sig[3], V[3][3];
-    if (!svd3(F, U, sig, V) || !(sig[2] > 0.f)) return false;
-    const float H[3] = {logf(sig[0]), logf(sig[1]), logf(sig[2])};
-    const float trH = H[0] + H[1] + H[2];
-    const float d[3] = {2.f * P.mu * H[0] + P.lambda * trH, 2.f * P.mu * H[1] + P.lambda * trH,
-                        2.f * P.mu * H[2] + P.lambda * trH};
-    t.xx = U[0][0] * U[0][0] * d[0] + U[0][1] * U[0][1] * d[1] + U[0][2] * U[0][2] * d[2];
-    t.yy = U[1][0] * U[1][0] * d[0] + U[1][1] * U[1][1] * d[1] + U[1][2] * U[1][2] * d[2];
-    t.zz = U[2][0] * U[2][0] * d[0] + U[2][1] * U[2][1] * d[1] + U[2][2] * U[2][2] * d[2];
-    t.xy = U[0][0] * U[1][0] * d[0] + U[0][1] * U[1][1] * d[1] + U[0][2] * U[1][2] * d[2];
-    t.xz = U[0][0] * U[2][0] * d[0] + U[0][1] * U[2][1] * d[1] + U[0][2] * U[2][2] * d[2];
-    t.yz = U[1][0] * U[2][0] * d[0] + U[1][1] * U[2][1] * d[1] + U[1][2] * U[2][2] * d[2];
+    const Sym X = left_cg_minus_i(F);
+    if (sym_norm2(X) <= MPM_SERIES_MAX * MPM_SERIES_MAX) {
+        if (!(det3(F) > 0.f)) return false;
+        hencky_stress_sym(P, hencky_series(X), t);
+        return true;
+    }
+    float U[3][3], eps[3];
+    if (!left_hencky(F, U, eps)) return false;
+    hencky_stress(P, U, eps, t);
     return true;
 }
 
@@ -688,7 +783,8 @@ struct Neighbours {
 // sums are factored over z: for each (a, b) the three z-nodes are first
 // reduced with w_z, dw_z and c w_z, then scattered into v_p, B_p and L_p.
 // MINB: CTAs of 256 threads per SM the registers are sized for (2: up to 128
-// registers a thread, 3: up to 80); the autotuner picks one per context.
+// registers a thread, 3: up to 80, 4: up to 64); the autotuner picks one per
+// context.
 // G2P of the particle at sorted position i (storage index p, block r).  With
 // STAGED its x, F, alpha and id come from a staging area (component k of
 // this thread at in[k * STG]: x 0-2, F 3-11, alpha 12, id 13), else from the
@@ -919,11 +1015,14 @@ cudaError_t launch_g2p(mpm_ctx* c) {
     const uint32_t* skey = c->pkey[c->sorted_sel];
     const int threads = c->tune.g2p_threads;
     const unsigned g = blocks_for(c->n, threads);
-    const bool two = c->tune.g2p_min_blocks == 2;
+    const int mb = c->tune.g2p_min_blocks;
 #define MPM_G2P(B_, D_, M_)                                                                                      \
     do {                                                                                                         \
-        if (two)                                                                                                 \
+        if (mb == 2)                                                                                             \
             k_g2p<B_, D_, M_, 2><<<g, threads, 0, c->ls>>>(ps, po, c->pstride, perm, skey, c->n, c->nbr, c->P,  \
+                                                           c->gv, c->dstat);                                     \
+        else if (mb == 4)                                                                                        \
+            k_g2p<B_, D_, M_, 4><<<g, threads, 0, c->ls>>>(ps, po, c->pstride, perm, skey, c->n, c->nbr, c->P,  \
                                                            c->gv, c->dstat);                                     \
         else                                                                                                     \
             k_g2p<B_, D_, M_, 3><<<g, threads, 0, c->ls>>>(ps, po, c->pstride, perm, skey, c->n, c->nbr, c->P,  \

@@ -69,6 +69,17 @@ def test_p2g_parity_per_particle_phi(oracle_mod):
     _check_p2g(o, wl, wl.x, wl.v, Cm, F, phi, keys, nodes, g, 4)
 
 
+@pytest.mark.parametrize("fscale", [0.003, 0.05])
+def test_p2g_parity_hencky_stress_both_forms(oracle_mod, fscale):
+    """The stored Hencky stress from the series form (||F F^T - I|| <= 1/16)
+    and from the eigenanalysis (above it)."""
+    wl, Cm, F = small_blob(n=4000, seed=16, material=W.DRUCKER_PRAGER, E=1e7, fscale=fscale)
+    o = oracle_for(wl)
+    sim = mpm.Simulation(mpm.config_from_workload(wl), wl.x, wl.v, Cm, F)
+    keys, nodes, g = _gpu_grid(sim, 4)
+    _check_p2g(o, wl, wl.x, wl.v, Cm, F, None, keys, nodes, g, 4)
+
+
 def test_p2g_dense_grid_matches_oracle(oracle_mod):
     wl, Cm, F = small_blob(n=3000, seed=13)
     o = oracle_for(wl)
@@ -134,8 +145,11 @@ def test_terrain_grid_update_parity(oracle_mod):
 
 
 @pytest.mark.parametrize("material", [W.NEOHOOKEAN, W.DRUCKER_PRAGER])
-def test_g2p_parity_from_gpu_grid(oracle_mod, material):
-    wl, Cm, F = small_blob(n=3000, seed=15, material=material, E=1e6, fscale=0.01, vscale=0.3, cscale=2.0)
+@pytest.mark.parametrize("fscale", [0.003, 0.01, 0.05])
+def test_g2p_parity_from_gpu_grid(oracle_mod, material, fscale):
+    # fscale 0.003 keeps ||F F^T - I|| below 1/16 (the series form of the
+    # return map), 0.05 above it (the eigenanalysis), 0.01 mixes both
+    wl, Cm, F = small_blob(n=3000, seed=15, material=material, E=1e6, fscale=fscale, vscale=0.3, cscale=2.0)
     o = oracle_for(wl)
     sim = mpm.Simulation(mpm.config_from_workload(wl), wl.x, wl.v, Cm, F)
     sim.rebuild_active()
