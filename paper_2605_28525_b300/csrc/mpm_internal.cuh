@@ -58,18 +58,23 @@ __device__ __forceinline__ void raise_flag(DevStatus* s, unsigned int* word, uns
     atomicOr(&s->abort, 1u);
 }
 
+// Status words that a kernel reads but that only earlier kernels write (or
+// that it may read stale, like the abort word) are read with plain, L1-cached
+// loads: writes of earlier kernels are visible at launch, and one address read
+// by every warp from L2 would serialise all of them on one L2 slice.
+
 // CTA-uniform test of the abort word at kernel entry.  Every thread of the
 // CTA must call it (it holds a barrier).
 __device__ __forceinline__ bool cta_aborted(const DevStatus* s) {
     __shared__ unsigned int ab;
-    if (threadIdx.x == 0) ab = *((volatile const unsigned int*)&s->abort);
+    if (threadIdx.x == 0) ab = s->abort;
     __syncthreads();
     return ab != 0u;
 }
 
 // Live active-block count, clamped to the capacity the arrays were sized for.
 __device__ __forceinline__ int64_t live_blocks(const DevStatus* s, int64_t cap) {
-    const int64_t n = (int64_t)*((volatile const unsigned int*)&s->n_active);
+    const int64_t n = (int64_t)s->n_active;
     return n < cap ? n : cap;
 }
 

@@ -21,7 +21,7 @@ constexpr unsigned FULL = 0xffffffffu;
 
 __device__ __forceinline__ int64_t live_count(const unsigned int* n_dev, int64_t n_cap,
                                               const unsigned int* abort) {
-    if (abort && *((volatile const unsigned int*)abort)) return 0;   // the step was abandoned
+    if (abort && *abort) return 0;   // the step was abandoned
     if (!n_dev) return n_cap;
     int64_t n = (int64_t)(*n_dev);
     return n < n_cap ? n : n_cap;

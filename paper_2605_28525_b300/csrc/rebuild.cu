@@ -40,7 +40,7 @@ namespace {
 __global__ void k_hash_clear(unsigned long long* __restrict__ keys, int* __restrict__ vals, int64_t H,
                              uint32_t* __restrict__ bmask, int64_t bwords, DevStatus* st) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool ab = *((volatile unsigned int*)&st->abort) != 0u;
+    const bool ab = st->abort != 0u;
     if (i == 0) st->go = ab ? 0u : 1u;
     if (ab) return;
     for (int64_t j = i; j < H; j += (int64_t)gridDim.x * blockDim.x) {
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(256) k_insert(const float* __restrict__ ps, in
     constexpr int S = (B == 4) ? 2 : 0;
     constexpr int R = (B == 4) ? 2 : 3;   // blocks a stencil can span per axis
     constexpr int NJ = R * R * R;
-    if (*((volatile unsigned int*)&st->go) == 0u) return;   // written by the clear before this kernel: uniform
+    if (st->go == 0u) return;   // written by the clear before this kernel: uniform
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
