@@ -162,26 +162,28 @@ __global__ void __launch_bounds__(256) k_insert(const float* __restrict__ ps, in
     // An ensemble's scenario s has its blocks ens_pitch * s further along x.
     if (P.n_scen > 1 && ok) b0[0] += scenario_of(P, __float_as_uint(ps[PID * stride + p])) * P.ens_pitch;
     // Lanes with the same base block form one group (particles are sorted, so
-    // a warp usually holds one or two groups).  The group's union of needed
-    // blocks is read from one ballot per block offset, and its members take
-    // the inserts in turn, so the CAS probes of one warp run in parallel.
+    // a warp usually holds one group).  The group's union of needed blocks is
+    // one OR reduction (one ballot per block offset when the warp holds several
+    // groups), and member r inserts offsets r, r + group size, ..., so the CAS
+    // probes of one warp run in parallel.
     const uint64_t key0 = ok ? pack_key(b0[0], b0[1], b0[2]) : EMPTY_KEY;
     const unsigned peers = __match_any_sync(FULL, key0);
     const int leader = __ffs(peers) - 1;
     const int rank = __popc(peers & ((1u << lane) - 1u));
     const int gsize = __popc(peers);
     unsigned gneed = 0;
+    if (peers == FULL) {
+        gneed = __reduce_or_sync(FULL, need);   // the usual case: one group per warp
+    } else {
 #pragma unroll
-    for (int j = 0; j < NJ; ++j)
-        if (__ballot_sync(FULL, (need >> j) & 1u) & peers) gneed |= 1u << j;
+        for (int j = 0; j < NJ; ++j)
+            if (__ballot_sync(FULL, (need >> j) & 1u) & peers) gneed |= 1u << j;
+    }
     int myslot = -1;
     if (ok) {
-        const int nneed = __popc(gneed);
-        for (int t = rank; t < nneed; t += gsize) {
-            // the t-th set bit of gneed
-            unsigned m = gneed;
-            for (int q = 0; q < t; ++q) m &= m - 1u;
-            const int j = __ffs(m) - 1;
+        // member `rank` takes block offsets rank, rank + gsize, ...
+        for (int j = rank; j < NJ; j += gsize) {
+            if (!((gneed >> j) & 1u)) continue;
             const int bi = b0[0] + j / (R * R), bj = b0[1] + (j / R) % R, bk = b0[2] + j % R;
             int slot;
             if (SCAN) {
@@ -192,7 +194,7 @@ __global__ void __launch_bounds__(256) k_insert(const float* __restrict__ ps, in
                 slot = hash_insert(hv, pack_key(bi, bj, bk), rel_key(P, bi, bj, bk), P.max_probe, akey, aslot, cap,
                                    bmask, st);
             }
-            if (j == 0) myslot = slot;   // bit 0 (the base block) is taken by rank 0 = the leader
+            if (j == 0) myslot = slot;   // offset 0 (the base block) is taken by rank 0 = the leader
         }
     }
     const int slot0 = __shfl_sync(FULL, myslot, leader);
@@ -452,23 +454,24 @@ __global__ void __launch_bounds__(128) k_interleave(const uint32_t* __restrict__
 
 // Sort key per particle and its rank among the particles of its (block, cell)
 // bin: lanes of a warp with the same key take consecutive ranks from one
-// atomic add by their leader.
-__global__ void __launch_bounds__(256) k_particle_bins(int64_t n, const uint32_t* __restrict__ pcode,
-                                                       HashView hv, int B3, int* __restrict__ bins,
-                                                       uint32_t* __restrict__ key, uint32_t* __restrict__ prank,
-                                                       DevStatus* st) {
-    if (cta_aborted(st)) return;
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31;
-    const unsigned FULL = 0xffffffffu;
-    uint32_t k = 0xffffffffu;
-    if (p < n) {
-        const uint32_t code = pcode[p];
-        const uint32_t q = code / (uint32_t)B3;
-        const int r = code == 0xffffffffu ? -1 : (hv.bits ? mask_rank(hv, q) : hv.vals[q]);
-        if (r < 0) raise_flag(st, &st->map_miss, 1u);
-        else k = (uint32_t)r * (uint32_t)B3 + code % (uint32_t)B3;
+// atomic add by their leader.  Each warp takes 64 consecutive particles, two
+// per lane, so that two chains of dependent loads are in flight per lane.
+__device__ __forceinline__ uint32_t bin_key(int64_t p, int64_t n, const uint32_t* __restrict__ pcode,
+                                            const HashView& hv, int B3, DevStatus* st) {
+    if (p >= n) return 0xffffffffu;
+    const uint32_t code = pcode[p];
+    const uint32_t q = code / (uint32_t)B3;
+    const int r = code == 0xffffffffu ? -1 : (hv.bits ? mask_rank(hv, q) : hv.vals[q]);
+    if (r < 0) {
+        raise_flag(st, &st->map_miss, 1u);
+        return 0xffffffffu;
     }
+    return (uint32_t)r * (uint32_t)B3 + code % (uint32_t)B3;
+}
+
+__device__ __forceinline__ void bin_rank(int64_t p, int64_t n, uint32_t k, int lane, int* __restrict__ bins,
+                                         uint32_t* __restrict__ key, uint32_t* __restrict__ prank) {
+    const unsigned FULL = 0xffffffffu;
     const unsigned peers = __match_any_sync(FULL, k);
     const int leader = __ffs(peers) - 1;
     int base = 0;
@@ -478,6 +481,18 @@ __global__ void __launch_bounds__(256) k_particle_bins(int64_t n, const uint32_t
         key[p] = k;
         prank[p] = (uint32_t)(base + __popc(peers & ((1u << lane) - 1u)));
     }
+}
+
+__global__ void __launch_bounds__(256) k_particle_bins(int64_t n, const uint32_t* __restrict__ pcode,
+                                                       HashView hv, int B3, int* __restrict__ bins,
+                                                       uint32_t* __restrict__ key, uint32_t* __restrict__ prank,
+                                                       DevStatus* st) {
+    if (cta_aborted(st)) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * 2 + lane, p1 = p0 + 32;
+    const uint32_t k0 = bin_key(p0, n, pcode, hv, B3, st), k1 = bin_key(p1, n, pcode, hv, B3, st);
+    bin_rank(p0, n, k0, lane, bins, key, prank);
+    bin_rank(p1, n, k1, lane, bins, key, prank);
 }
 
 constexpr int SC_THREADS = 256, SC_ITEMS = 8, SC_TILE = SC_THREADS * SC_ITEMS;
@@ -607,18 +622,31 @@ __global__ void k_scan_add_n(int* __restrict__ cs, int64_t n, const DevStatus* s
     if (i == n) cs[n] = tsum[ntiles];
 }
 
-// Scatter into (block, cell) order.
-__global__ void k_bin_scatter(int64_t n, const uint32_t* __restrict__ key, const uint32_t* __restrict__ prank,
-                              const int* __restrict__ cs, uint32_t* __restrict__ skey, uint32_t* __restrict__ perm,
-                              const DevStatus* st) {
+// Scatter into (block, cell) order, two particles per thread (p and p + 32
+// within the warp's 64) for two load chains in flight.
+__global__ void __launch_bounds__(256) k_bin_scatter(int64_t n, const uint32_t* __restrict__ key,
+                                                     const uint32_t* __restrict__ prank, const int* __restrict__ cs,
+                                                     uint32_t* __restrict__ skey, uint32_t* __restrict__ perm,
+                                                     const DevStatus* st) {
     if (cta_aborted(st)) return;
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    const uint32_t k = key[p];
-    if (k == 0xffffffffu) return;
-    const int pos = cs[k] + (int)prank[p];
-    skey[pos] = k;
-    perm[pos] = (uint32_t)p;
+    const int lane = threadIdx.x & 31;
+    const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * 2 + lane;
+    uint32_t k[2] = {0xffffffffu, 0xffffffffu}, r[2] = {0u, 0u};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int64_t p = p0 + 32 * h;
+        if (p < n) {
+            k[h] = key[p];
+            r[h] = prank[p];
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (k[h] == 0xffffffffu) continue;
+        const int pos = cs[k[h]] + (int)r[h];
+        skey[pos] = k[h];
+        perm[pos] = (uint32_t)(p0 + 32 * h);
+    }
 }
 
 // Particle range and flag of every active block from the cell starts.
@@ -746,13 +774,13 @@ cudaError_t launch_particle_keys(mpm_ctx* c) {
     const int64_t nkeys = cap * c->B3;
     if (counting_sort(c)) {
         // one pass: key + rank in bin; scan of the bins; scatter
-        k_particle_bins<<<blocks_for(c->n, 256), 256, 0, c->ls>>>(c->n, c->pcode, hash_view(c), c->B3, c->bins, c->pkey[0],
+        k_particle_bins<<<blocks_for(c->n, 512), 256, 0, c->ls>>>(c->n, c->pcode, hash_view(c), c->B3, c->bins, c->pkey[0],
                                                                   c->prank, c->dstat);
         const int ntiles = (int)((nkeys + SC_TILE - 1) / SC_TILE);
         k_scan_tiles<<<ntiles, SC_THREADS, 0, c->ls>>>(c->bins, cap, c->B3, c->dstat, c->cs, c->tsum);
         k_scan_sums<<<1, 1024, 0, c->ls>>>(c->tsum, ntiles, c->dstat);
         k_scan_add<<<blocks_for(nkeys + 1, 256), 256, 0, c->ls>>>(c->cs, cap, c->B3, c->dstat, c->tsum, ntiles);
-        k_bin_scatter<<<blocks_for(c->n, 256), 256, 0, c->ls>>>(c->n, c->pkey[0], c->prank, c->cs, c->pkey[1],
+        k_bin_scatter<<<blocks_for(c->n, 512), 256, 0, c->ls>>>(c->n, c->pkey[0], c->prank, c->cs, c->pkey[1],
                                                                 c->pval[1], c->dstat);
         c->launches += 5;
         c->sorted_sel = 1;
