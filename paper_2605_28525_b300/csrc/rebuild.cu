@@ -104,12 +104,11 @@ __device__ int hash_insert(const HashView& hv, uint64_t key, uint32_t rkey, int 
 
 // Reads x, checks it and computes the stencil base node; false if the
 // particle is unusable (flags set).
-__device__ __forceinline__ bool particle_base(const float* __restrict__ ps, int64_t stride, int64_t p,
-                                              const Params& P, int base[3], DevStatus* st) {
+__device__ __forceinline__ bool particle_base_x(const float x[3], const Params& P, int base[3], DevStatus* st) {
     bool ok = true;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        float fx = ps[(PX + a) * stride + p] * P.inv_h;
+        float fx = x[a] * P.inv_h;
         if (!isfinite(fx)) {
             raise_flag(st, &st->numeric, 1u);
             ok = false;
@@ -128,25 +127,31 @@ __device__ __forceinline__ bool particle_base(const float* __restrict__ ps, int6
     return ok;
 }
 
+__device__ __forceinline__ bool particle_base(const float* __restrict__ ps, int64_t stride, int64_t p,
+                                              const Params& P, int base[3], DevStatus* st) {
+    const float x[3] = {ps[(PX + 0) * stride + p], ps[(PX + 1) * stride + p], ps[(PX + 2) * stride + p]};
+    return particle_base_x(x, P, base, st);
+}
+
 // SCAN: the scan realisation (Sec. 4.2, Alg. 2): each needed block's bit is
 // set in the mask and the particle's code holds its base block's relative key;
 // no table.  Otherwise Alg. 6 as above, and the code holds the table slot.
+// One particle p (coordinates x already loaded when p < n); every lane of the
+// warp calls it.
 template <int B, bool SCAN>
-__global__ void __launch_bounds__(256) k_insert(const float* __restrict__ ps, int64_t stride, int64_t n,
-                                                Params P, HashView hv, uint32_t* __restrict__ akey,
-                                                uint32_t* __restrict__ aslot, int64_t cap,
-                                                uint32_t* __restrict__ bmask, uint32_t* __restrict__ pcode,
-                                                DevStatus* st) {
+__device__ __forceinline__ void insert_particle(const float* __restrict__ ps, int64_t stride, int64_t n, int64_t p,
+                                                const float x[3], const Params& P, const HashView& hv,
+                                                uint32_t* __restrict__ akey, uint32_t* __restrict__ aslot,
+                                                int64_t cap, uint32_t* __restrict__ bmask,
+                                                uint32_t* __restrict__ pcode, DevStatus* st) {
     constexpr int S = (B == 4) ? 2 : 0;
     constexpr int R = (B == 4) ? 2 : 3;   // blocks a stencil can span per axis
     constexpr int NJ = R * R * R;
-    if (st->go == 0u) return;   // written by the clear before this kernel: uniform
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
     int base[3] = {0, 0, 0};
     bool ok = p < n;
-    if (ok) ok = particle_base(ps, stride, p, P, base, st);
+    if (ok) ok = particle_base_x(x, P, base, st);
     int b0[3];
     unsigned need = 0;   // bit j: block b0 + (j / R^2, (j / R) % R, j % R) holds a stencil node
 #pragma unroll
@@ -202,6 +207,28 @@ __global__ void __launch_bounds__(256) k_insert(const float* __restrict__ ps, in
         const int cell = (base[0] & (B - 1)) + B * ((base[1] & (B - 1)) + B * (base[2] & (B - 1)));
         pcode[p] = slot0 < 0 ? 0xffffffffu : (uint32_t)slot0 * (uint32_t)(B * B * B) + (uint32_t)cell;
     }
+}
+
+// Each warp takes 64 consecutive particles, p and p + 32 per lane; both
+// particles' coordinates are loaded before the first one's probes, so the
+// second load overlaps them.
+template <int B, bool SCAN>
+__global__ void __launch_bounds__(256) k_insert(const float* __restrict__ ps, int64_t stride, int64_t n,
+                                                Params P, HashView hv, uint32_t* __restrict__ akey,
+                                                uint32_t* __restrict__ aslot, int64_t cap,
+                                                uint32_t* __restrict__ bmask, uint32_t* __restrict__ pcode,
+                                                DevStatus* st) {
+    if (st->go == 0u) return;   // written by the clear before this kernel: uniform
+    const int lane = threadIdx.x & 31;
+    const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * 2 + lane, p1 = p0 + 32;
+    float x0[3] = {0.f, 0.f, 0.f}, x1[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (p0 < n) x0[a] = ps[(PX + a) * stride + p0];
+        if (p1 < n) x1[a] = ps[(PX + a) * stride + p1];
+    }
+    insert_particle<B, SCAN>(ps, stride, n, p0, x0, P, hv, akey, aslot, cap, bmask, pcode, st);
+    insert_particle<B, SCAN>(ps, stride, n, p1, x1, P, hv, akey, aslot, cap, bmask, pcode, st);
 }
 
 // Dense comparator: the identity map.  The particle's sort key is the block's
@@ -690,7 +717,7 @@ cudaError_t launch_insert(mpm_ctx* c, int64_t ins_cap) {
     c->launches += 2;
     const float* ps = c->ps[c->cur];
 #define MPM_INS(B_, S_)                                                                                           \
-    k_insert<B_, S_><<<blocks_for(c->n, 256), 256, 0, c->ls>>>(ps, c->pstride, c->n, c->P, hv, c->akey[0],       \
+    k_insert<B_, S_><<<blocks_for(c->n, 512), 256, 0, c->ls>>>(ps, c->pstride, c->n, c->P, hv, c->akey[0],       \
                                                                c->aslot[0], ins_cap, c->bmask, c->pcode, c->dstat)
     if (c->B == 4) {
         if (c->scan) MPM_INS(4, true);
