@@ -535,7 +535,7 @@ def main():
             "config": dict(wl.describe(), l2=l2_note, step_launch="one mpm_step call of K steps (CUDA graphs)"
                            if flush is None else "mpm_step(1) per step",
                            parallelism="replicas" if ws > 1 else "single GPU", compaction=args.compaction,
-                           tuning={k: tuning[k] for k in ("p2g_ctas_per_sm", "g2p_threads", "g2p_min_blocks")},
+                           tuning={k: tuning[k] for k in ("p2g_ctas_per_sm", "g2p_threads", "g2p_regs")},
                            active_blocks=st["n_active_blocks"], particle_blocks=st["n_particle_blocks"]),
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,

@@ -974,7 +974,7 @@ void fill_tuning(const mpm_ctx* c, mpm_tuning* o) {
     std::memset(o, 0, sizeof(*o));
     o->p2g_ctas_per_sm = c->tune.p2g_ctas_per_sm;
     o->g2p_threads = c->tune.g2p_threads;
-    o->g2p_min_blocks = c->tune.g2p_min_blocks;
+    o->g2p_regs = c->tune.g2p_regs;
 }
 
 // Median of the device times of `repeats` runs of `run` (each bracketed by
@@ -1046,22 +1046,22 @@ mpm_status mpm_autotune(mpm_ctx* c, int32_t repeats, mpm_tuning* out) {
     CK(launch_p2g(c));
     CK(launch_grid_update(c));
     // G2P reads the current buffer and writes the other one: reruns repeat it
-    for (int threads = 128; threads <= 256; threads *= 2)
-        for (int mb = 2; mb <= 4; ++mb) {
-            c->tune.g2p_threads = threads;
-            c->tune.g2p_min_blocks = mb;
-            double ms = 0;
-            s = time_median(c, repeats, []() { return cudaSuccess; }, [&]() { return launch_g2p(c); }, &ms);
-            if (s != MPM_OK) {
-                c->tune = keep;
-                return s;
-            }
-            if (ms < best_g2p) {
-                best_g2p = ms;
-                best.g2p_threads = threads;
-                best.g2p_min_blocks = mb;
-            }
+    static const int shapes[][2] = {{128, 72}, {128, 80}, {128, 128}, {256, 80}, {256, 128}};
+    for (const auto& sh : shapes) {
+        c->tune.g2p_threads = sh[0];
+        c->tune.g2p_regs = sh[1];
+        double ms = 0;
+        s = time_median(c, repeats, []() { return cudaSuccess; }, [&]() { return launch_g2p(c); }, &ms);
+        if (s != MPM_OK) {
+            c->tune = keep;
+            return s;
         }
+        if (ms < best_g2p) {
+            best_g2p = ms;
+            best.g2p_threads = sh[0];
+            best.g2p_regs = sh[1];
+        }
+    }
     c->tune = best;
     c->phase = 0;          // the timed step is discarded; the state is the one before it
     ++c->cap_version;      // captured steps hold the old launch shapes
@@ -1082,12 +1082,13 @@ mpm_status mpm_get_tuning(mpm_ctx* c, mpm_tuning* out) {
 mpm_status mpm_set_tuning(mpm_ctx* c, const mpm_tuning* in) {
     if (!c || !in) return MPM_ERR_INVALID_ARG;
     if (in->p2g_ctas_per_sm < 1 || in->p2g_ctas_per_sm > 8 || (in->g2p_threads != 128 && in->g2p_threads != 256) ||
-        in->g2p_min_blocks < 2 || in->g2p_min_blocks > 4)
+        (in->g2p_regs != 72 && in->g2p_regs != 80 && in->g2p_regs != 128) ||
+        (in->g2p_regs == 72 && in->g2p_threads != 128))
         return fail(c, MPM_ERR_INVALID_ARG, "tuning outside p2g_ctas_per_sm 1..8, g2p_threads 128/256, "
-                                            "g2p_min_blocks 2..4");
+                                            "g2p_regs 72 (128 threads only), 80, 128");
     c->tune.p2g_ctas_per_sm = in->p2g_ctas_per_sm;
     c->tune.g2p_threads = in->g2p_threads;
-    c->tune.g2p_min_blocks = in->g2p_min_blocks;
+    c->tune.g2p_regs = in->g2p_regs;
     ++c->cap_version;
     return MPM_OK;
 }

@@ -233,8 +233,8 @@ __device__ __forceinline__ void bspline_a(float d, int a, float& w, float& dw) {
 // Launch shapes that change no result (mpm_autotune picks them).
 struct Tuning {
     int p2g_ctas_per_sm = MPM_P2G_MAX_CTAS;   // persistent P2G grid: 148 x this many CTAs of 128 threads
-    int g2p_threads = 256;       // G2P CTA size (128 or 256)
-    int g2p_min_blocks = 3;      // G2P register budget: 3 (80 registers) or 2 (128) CTAs of 256 per SM
+    int g2p_threads = 128;       // G2P CTA size (128 or 256)
+    int g2p_regs = 72;           // registers a G2P thread is compiled for: 72 (128 threads only), 80, 128
 };
 
 struct RadixScratch {

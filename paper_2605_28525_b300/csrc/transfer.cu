@@ -782,9 +782,9 @@ struct Neighbours {
 // neighbour table (L1-resident for the particles of one block).  The node
 // sums are factored over z: for each (a, b) the three z-nodes are first
 // reduced with w_z, dw_z and c w_z, then scattered into v_p, B_p and L_p.
-// MINB: CTAs of 256 threads per SM the registers are sized for (2: up to 128
-// registers a thread, 3: up to 80, 4: up to 64); the autotuner picks one per
-// context.
+// THREADS x REGS: the CTA size and the registers a thread is compiled for
+// (at most REGS: 65536 / (THREADS x REGS) CTAs fit on an SM); the autotuner
+// picks one pair per context.
 // G2P of the particle at sorted position i (storage index p, block r).  With
 // STAGED its x, F, alpha and id come from a staging area (component k of
 // this thread at in[k * STG]: x 0-2, F 3-11, alpha 12, id 13), else from the
@@ -917,8 +917,8 @@ __device__ __forceinline__ void g2p_particle(const float* __restrict__ ps, float
     po[PID * stride + i] = STAGED ? in[13 * STG] : ps[PID * stride + p];
 }
 
-template <int B, bool DENSE, int MAT, int MINB>
-__global__ void __launch_bounds__(256, MINB) k_g2p(const float* __restrict__ ps, float* __restrict__ po, int64_t stride,
+template <int B, bool DENSE, int MAT, int THREADS, int REGS>
+__global__ void __launch_bounds__(THREADS, 65536 / (THREADS * REGS)) k_g2p(const float* __restrict__ ps, float* __restrict__ po, int64_t stride,
                                               const uint32_t* __restrict__ perm, const uint32_t* __restrict__ skey,
                                               int64_t n, const int* __restrict__ nbr, Params P,
                                               const float4* __restrict__ gv, DevStatus* st) {
@@ -1013,20 +1013,21 @@ cudaError_t launch_g2p(mpm_ctx* c) {
     float* po = c->ps[1 - c->cur];
     const uint32_t* perm = c->pval[c->sorted_sel];
     const uint32_t* skey = c->pkey[c->sorted_sel];
-    const int threads = c->tune.g2p_threads;
+    const int threads = c->tune.g2p_threads, regs = c->tune.g2p_regs;
     const unsigned g = blocks_for(c->n, threads);
-    const int mb = c->tune.g2p_min_blocks;
+#define MPM_G2P_TR(B_, D_, M_, T_, R_)                                                                          \
+    k_g2p<B_, D_, M_, T_, R_><<<g, T_, 0, c->ls>>>(ps, po, c->pstride, perm, skey, c->n, c->nbr, c->P, c->gv,   \
+                                                  c->dstat)
 #define MPM_G2P(B_, D_, M_)                                                                                      \
     do {                                                                                                         \
-        if (mb == 2)                                                                                             \
-            k_g2p<B_, D_, M_, 2><<<g, threads, 0, c->ls>>>(ps, po, c->pstride, perm, skey, c->n, c->nbr, c->P,  \
-                                                           c->gv, c->dstat);                                     \
-        else if (mb == 4)                                                                                        \
-            k_g2p<B_, D_, M_, 4><<<g, threads, 0, c->ls>>>(ps, po, c->pstride, perm, skey, c->n, c->nbr, c->P,  \
-                                                           c->gv, c->dstat);                                     \
-        else                                                                                                     \
-            k_g2p<B_, D_, M_, 3><<<g, threads, 0, c->ls>>>(ps, po, c->pstride, perm, skey, c->n, c->nbr, c->P,  \
-                                                           c->gv, c->dstat);                                     \
+        if (threads == 256) {                                                                                    \
+            if (regs == 128) MPM_G2P_TR(B_, D_, M_, 256, 128);                                                   \
+            else MPM_G2P_TR(B_, D_, M_, 256, 80);                                                                \
+        } else {                                                                                                 \
+            if (regs == 128) MPM_G2P_TR(B_, D_, M_, 128, 128);                                                   \
+            else if (regs == 80) MPM_G2P_TR(B_, D_, M_, 128, 80);                                                \
+            else MPM_G2P_TR(B_, D_, M_, 128, 72);                                                                \
+        }                                                                                                        \
     } while (0)
     const int mat = c->P.material;
     if (c->B == 4) {
@@ -1047,6 +1048,7 @@ cudaError_t launch_g2p(mpm_ctx* c) {
         }
     }
 #undef MPM_G2P
+#undef MPM_G2P_TR
     ++c->launches;
     return cudaGetLastError();
 }

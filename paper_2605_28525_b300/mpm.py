@@ -68,7 +68,7 @@ class Stats(C.Structure):
 
 
 class Tuning(C.Structure):
-    _fields_ = [("p2g_ctas_per_sm", C.c_int32), ("g2p_threads", C.c_int32), ("g2p_min_blocks", C.c_int32),
+    _fields_ = [("p2g_ctas_per_sm", C.c_int32), ("g2p_threads", C.c_int32), ("g2p_regs", C.c_int32),
                 ("reserved", C.c_int32), ("p2g_ms", C.c_double), ("g2p_ms", C.c_double)]
 
     def as_dict(self):
@@ -299,8 +299,8 @@ class Simulation:
         _check(lib().mpm_get_tuning(self.h, C.byref(t)), self.h)
         return t.as_dict()
 
-    def set_tuning(self, p2g_ctas_per_sm: int, g2p_threads: int, g2p_min_blocks: int):
-        t = Tuning(p2g_ctas_per_sm, g2p_threads, g2p_min_blocks, 0, 0.0, 0.0)
+    def set_tuning(self, p2g_ctas_per_sm: int, g2p_threads: int, g2p_regs: int):
+        t = Tuning(p2g_ctas_per_sm, g2p_threads, g2p_regs, 0, 0.0, 0.0)
         _check(lib().mpm_set_tuning(self.h, C.byref(t)), self.h)
 
     # ---- checkpoints and the adjoint (device buffers: torch CUDA tensors)
