@@ -510,16 +510,68 @@ __device__ __forceinline__ void bin_rank(int64_t p, int64_t n, uint32_t k, int l
     }
 }
 
+// The 512 particles of a CTA are consecutive in the previous step's sorted
+// order, so their keys usually span a few blocks' bins: when the span fits
+// BIN_SPAN, the CTA counts them in shared memory and adds one total per
+// distinct bin to the global counts (a particle's rank = the bin's global
+// base + its shared-memory rank); otherwise every particle takes the
+// warp-aggregated global path.
+constexpr int BIN_SPAN = 2048;
+
 __global__ void __launch_bounds__(256) k_particle_bins(int64_t n, const uint32_t* __restrict__ pcode,
                                                        HashView hv, int B3, int* __restrict__ bins,
                                                        uint32_t* __restrict__ key, uint32_t* __restrict__ prank,
                                                        DevStatus* st) {
+    __shared__ int hist[BIN_SPAN];
+    __shared__ uint32_t wmin[8], wmax[8];
     if (cta_aborted(st)) return;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * 2 + lane, p1 = p0 + 32;
     const uint32_t k0 = bin_key(p0, n, pcode, hv, B3, st), k1 = bin_key(p1, n, pcode, hv, B3, st);
-    bin_rank(p0, n, k0, lane, bins, key, prank);
-    bin_rank(p1, n, k1, lane, bins, key, prank);
+    // key range of the CTA's valid keys (invalid keys are all ones)
+    const uint32_t lo = min(k0, k1);
+    const uint32_t hi = max(k0 == 0xffffffffu ? 0u : k0, k1 == 0xffffffffu ? 0u : k1);
+    const uint32_t wl = __reduce_min_sync(0xffffffffu, lo), wh = __reduce_max_sync(0xffffffffu, hi);
+    if (lane == 0) {
+        wmin[w] = wl;
+        wmax[w] = wh;
+    }
+    for (int i = threadIdx.x; i < BIN_SPAN; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    uint32_t kmin = 0xffffffffu, kmax = 0u;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        kmin = min(kmin, wmin[i]);
+        kmax = max(kmax, wmax[i]);
+    }
+    if (kmin == 0xffffffffu) {       // no valid key in this CTA
+        if (p0 < n) key[p0] = 0xffffffffu;
+        if (p1 < n) key[p1] = 0xffffffffu;
+        return;
+    }
+    if (kmax - kmin >= (uint32_t)BIN_SPAN) {   // CTA-uniform: the global path
+        bin_rank(p0, n, k0, lane, bins, key, prank);
+        bin_rank(p1, n, k1, lane, bins, key, prank);
+        return;
+    }
+    int r0 = 0, r1 = 0;
+    if (k0 != 0xffffffffu) r0 = atomicAdd(&hist[k0 - kmin], 1);
+    if (k1 != 0xffffffffu) r1 = atomicAdd(&hist[k1 - kmin], 1);
+    __syncthreads();
+    const int span = (int)(kmax - kmin) + 1;
+    for (int i = threadIdx.x; i < span; i += blockDim.x) {
+        const int c = hist[i];
+        if (c > 0) hist[i] = atomicAdd(&bins[kmin + i], c);   // the bin's global base for this CTA
+    }
+    __syncthreads();
+    if (p0 < n) {
+        key[p0] = k0;
+        if (k0 != 0xffffffffu) prank[p0] = (uint32_t)(hist[k0 - kmin] + r0);
+    }
+    if (p1 < n) {
+        key[p1] = k1;
+        if (k1 != 0xffffffffu) prank[p1] = (uint32_t)(hist[k1 - kmin] + r1);
+    }
 }
 
 constexpr int SC_THREADS = 256, SC_ITEMS = 8, SC_TILE = SC_THREADS * SC_ITEMS;
