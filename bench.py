@@ -436,6 +436,8 @@ def main():
     ap.add_argument("--adjoint-iters", type=int, default=50)
     ap.add_argument("--sweep", action="store_true",
                     help="add the sparse-vs-dense occupancy sweep of the 1M column (boxes 128..1024 wide)")
+    ap.add_argument("--tuning", default=None,
+                    help="launch shapes p2g_ctas_per_sm,g2p_threads,g2p_regs instead of the autotuner's choice")
     ap.add_argument("--compaction", default="hash", choices=["hash", "scan"],
                     help="active-set realisation: the hash (Sec. 4.3) or the scan (Sec. 4.2)")
     args = ap.parse_args()
@@ -464,7 +466,11 @@ def main():
     sim = mpm.Simulation.from_workload(wl, flags=cflags, stream=stream, device_inputs=True)
     for _ in range(args.warmup):
         sim.step(1)
-    tuning = sim.autotune(3)        # the library's own autotuner: launch shapes only, no result changes
+    if args.tuning:                 # fixed launch shapes (e.g. under a profiler, where the autotuner's timing is off)
+        sim.set_tuning(*(int(v) for v in args.tuning.split(",")))
+        tuning = sim.tuning()
+    else:
+        tuning = sim.autotune(3)    # the library's own autotuner: launch shapes only, no result changes
     sim.step(1)                     # recapture the step graphs with the chosen shapes
     torch.cuda.synchronize()
     launches0 = sim.stats()["kernel_launches"]

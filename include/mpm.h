@@ -249,7 +249,7 @@ typedef struct mpm_tuning {
 } mpm_tuning;
 
 /* Autotuner: runs one rebuild on the current state, then times P2G for each
- * even p2g_ctas_per_sm up to the most that fit on an SM, and G2P for each
+ * p2g_ctas_per_sm from 1 to the most that fit on an SM, and G2P for each
  * (g2p_threads, g2p_regs) in
  * {(128, 72), (128, 80), (128, 128), (256, 80), (256, 128)}, `repeats` times each (CUDA events on the context's
  * stream; the grid is cleared before every P2G), and keeps the shapes with

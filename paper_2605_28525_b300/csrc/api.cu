@@ -1028,7 +1028,7 @@ mpm_status mpm_autotune(mpm_ctx* c, int32_t repeats, mpm_tuning* out) {
     const Tuning keep = c->tune;
     double best_p2g = 1e30, best_g2p = 1e30;
     Tuning best = keep;
-    for (int k = 2; k <= MPM_P2G_MAX_CTAS; k += 2) {
+    for (int k = 1; k <= MPM_P2G_MAX_CTAS; ++k) {
         c->tune.p2g_ctas_per_sm = k;
         double ms = 0;
         s = time_median(c, repeats, p2g_prep, [&]() { return launch_p2g(c); }, &ms);

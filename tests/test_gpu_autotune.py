@@ -20,7 +20,7 @@ def test_autotune_keeps_state_and_results(oracle_mod):
     b.step(2)
     before = _bits(a)
     t = a.autotune(repeats=3)
-    assert 2 <= t["p2g_ctas_per_sm"] <= 4 and t["g2p_threads"] in (128, 256) and (t["g2p_threads"], t["g2p_regs"]) in ((128, 72), (128, 80), (128, 128), (256, 80), (256, 128))
+    assert 1 <= t["p2g_ctas_per_sm"] <= 4 and t["g2p_threads"] in (128, 256) and (t["g2p_threads"], t["g2p_regs"]) in ((128, 72), (128, 80), (128, 128), (256, 80), (256, 128))
     assert t["p2g_ms"] > 0 and t["g2p_ms"] > 0
     assert a.tuning()["g2p_threads"] == t["g2p_threads"]
     after = _bits(a)
