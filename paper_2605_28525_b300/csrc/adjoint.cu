@@ -338,6 +338,230 @@ __device__ double hencky_adjoint(const float Ff[9], const float tb[9], double mu
     return 2.0 * (T[0][0] * ls[0] + T[1][1] * ls[1] + T[2][2] * ls[2]) * dmu + (T[0][0] + T[1][1] + T[2][2]) * trl * dla;
 }
 
+// ---- the series forms (the forward's path when ||F F^T - I||_F <= 1/16)
+//
+// The forward evaluates the Hencky strain as eps = ln(I + X) / 2, X = F F^T - I,
+// by a fifth-order power series and the projected F as exp(Y) F_tr by a
+// fourth-order one, both in Horner form.  Their adjoints below run the same
+// Horner steps backwards in FP32: every step is a matrix product, so there is
+// no divided difference of singular values to lose precision in.  Matrices
+// are full 3x3, row-major.
+
+constexpr float ADJ_SERIES_MAX2 = 0.0625f * 0.0625f;   // the forward's threshold, squared
+
+__device__ __forceinline__ void mm3(const float A[9], const float B[9], float C[9]) {   // C = A B
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) C[i * 3 + j] = A[i * 3] * B[j] + A[i * 3 + 1] * B[3 + j] + A[i * 3 + 2] * B[6 + j];
+}
+
+__device__ __forceinline__ void mm3_add(const float A[9], const float B[9], float s, float C[9]) {   // C += s A B
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            C[i * 3 + j] += s * (A[i * 3] * B[j] + A[i * 3 + 1] * B[3 + j] + A[i * 3 + 2] * B[6 + j]);
+}
+
+__device__ __forceinline__ void axpi3(const float A[9], float s, float d, float C[9]) {   // C = s A + d I
+#pragma unroll
+    for (int k = 0; k < 9; ++k) C[k] = s * A[k] + ((k % 4 == 0) ? d : 0.f);
+}
+
+// X = F F^T - I (diagonal as (F_ii - 1)(F_ii + 1) + the other two squares)
+// and its squared Frobenius norm.
+__device__ __forceinline__ float cg_minus_i(const float F[9], float X[9]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            if (i == j) {
+                const int a = (i + 1) % 3, b = (i + 2) % 3;
+                X[i * 4] = fmaf(F[i * 4] - 1.f, F[i * 4] + 1.f, F[i * 3 + a] * F[i * 3 + a] + F[i * 3 + b] * F[i * 3 + b]);
+            } else {
+                X[i * 3 + j] = F[i * 3] * F[j * 3] + F[i * 3 + 1] * F[j * 3 + 1] + F[i * 3 + 2] * F[j * 3 + 2];
+            }
+        }
+    float n2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) n2 += X[k] * X[k];
+    return n2;
+}
+
+// Forward: eps = q4 X / 2 with q1 = X/5 - I/4, q2 = q1 X + I/3,
+// q3 = q2 X - I/2, q4 = q3 X + I (the intermediates are kept for the adjoint).
+struct LogSeries {
+    float q1[9], q2[9], q3[9], q4[9];
+    __device__ __forceinline__ void eval(const float X[9], float eps[9]) {
+        float t[9];
+        axpi3(X, 0.2f, -0.25f, q1);
+        mm3(q1, X, t);
+        axpi3(t, 1.f, 1.f / 3.f, q2);
+        mm3(q2, X, t);
+        axpi3(t, 1.f, -0.5f, q3);
+        mm3(q3, X, t);
+        axpi3(t, 1.f, 1.f, q4);
+        mm3(q4, X, t);
+        axpi3(t, 0.5f, 0.f, eps);
+    }
+    // Xbar from epsbar (C = A B gives Abar = Cbar B^T, Bbar = A^T Cbar; all
+    // forward matrices are symmetric)
+    __device__ __forceinline__ void adjoint(const float X[9], const float eb[9], float Xb[9]) const {
+        float b4[9], b3[9], b2[9], b1[9];
+        mm3(eb, X, b4);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) b4[k] *= 0.5f;
+        mm3(q4, eb, Xb);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Xb[k] *= 0.5f;
+        mm3(b4, X, b3);
+        mm3_add(q3, b4, 1.f, Xb);
+        mm3(b3, X, b2);
+        mm3_add(q2, b3, 1.f, Xb);
+        mm3(b2, X, b1);
+        mm3_add(q1, b2, 1.f, Xb);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Xb[k] += 0.2f * b1[k];
+    }
+};
+
+// Forward: E = I + Y e3, e3 = I + Y e2 / 2, e2 = I + Y e1 / 3, e1 = I + Y / 4.
+struct ExpSeries {
+    float e1[9], e2[9], e3[9];
+    __device__ __forceinline__ void eval(const float Y[9], float E[9]) {
+        float t[9];
+        axpi3(Y, 0.25f, 1.f, e1);
+        mm3(Y, e1, t);
+        axpi3(t, 1.f / 3.f, 1.f, e2);
+        mm3(Y, e2, t);
+        axpi3(t, 0.5f, 1.f, e3);
+        mm3(Y, e3, t);
+        axpi3(t, 1.f, 1.f, E);
+    }
+    __device__ __forceinline__ void adjoint(const float Y[9], const float Eb[9], float Yb[9]) const {
+        float b3[9], b2[9], b1[9];
+        mm3(Eb, e3, Yb);
+        mm3(Y, Eb, b3);
+        mm3_add(b3, e2, 0.5f, Yb);
+        mm3(Y, b3, b2);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) b2[k] *= 0.5f;
+        mm3_add(b2, e1, 1.f / 3.f, Yb);
+        mm3(Y, b2, b1);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Yb[k] += 0.25f * (1.f / 3.f) * b1[k];
+    }
+};
+
+// Fbar += (Xbar + Xbar^T) F, the adjoint of X = F F^T - I.
+__device__ __forceinline__ void cg_adjoint(const float F[9], const float Xb[9], float Fb[9]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            float v = 0.f;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) v += (Xb[i * 3 + k] + Xb[k * 3 + i]) * F[k * 3 + j];
+            Fb[i * 3 + j] += v;
+        }
+}
+
+// The return map's adjoint in the series form: Fbar_tr and dL/dalpha from
+// Fbar' (the same contract as dp_map_adjoint).  False outside the series
+// range or for det F_tr <= 0.
+__device__ bool dp_map_adjoint_series(const float Ftr[9], float alpha, float kappa, const float Fb[9], float Fb_tr[9],
+                                      double* abar) {
+    float X[9];
+    if (!(cg_minus_i(Ftr, X) <= ADJ_SERIES_MAX2)) return false;
+    const float J = Ftr[0] * (Ftr[4] * Ftr[8] - Ftr[5] * Ftr[7]) - Ftr[1] * (Ftr[3] * Ftr[8] - Ftr[5] * Ftr[6]) +
+                    Ftr[2] * (Ftr[3] * Ftr[7] - Ftr[4] * Ftr[6]);
+    if (!(J > 0.f)) return false;
+    LogSeries ls;
+    float e[9];
+    ls.eval(X, e);
+    const float tr = e[0] + e[4] + e[8];
+    float dev[9];
+    axpi3(e, 1.f, -tr / 3.f, dev);
+    float nd2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) nd2 += dev[k] * dev[k];
+    const float nd = sqrtf(nd2);
+    const float dgam = nd + kappa * tr * alpha;
+    *abar = 0.0;
+    if (tr < 0.f && dgam <= 0.f) {   // inside the cone: F' = F_tr
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Fb_tr[k] = Fb[k];
+        return true;
+    }
+    const bool tip = tr >= 0.f;
+    const float kk = tip ? 0.f : dgam / nd;
+    float Y[9];
+    if (tip) axpi3(e, -1.f, 0.f, Y);
+    else axpi3(dev, -kk, 0.f, Y);
+    ExpSeries es;
+    float E[9];
+    es.eval(Y, E);
+    // F' = E F_tr: Fbar_tr = E^T Fbar' = E Fbar', Ebar = Fbar' F_tr^T
+    mm3(E, Fb, Fb_tr);
+    float Eb[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            Eb[i * 3 + j] = Fb[i * 3] * Ftr[j * 3] + Fb[i * 3 + 1] * Ftr[j * 3 + 1] + Fb[i * 3 + 2] * Ftr[j * 3 + 2];
+    float Yb[9];
+    es.adjoint(Y, Eb, Yb);
+    float eb[9];
+    if (tip) {
+        axpi3(Yb, -1.f, 0.f, eb);                    // Y = -eps
+    } else {
+        // Y = -k dev, k = 1 + kappa alpha tr / nd, nd = ||dev||, dev = eps - tr/3 I
+        float kb = 0.f;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) kb -= Yb[k] * dev[k];
+        const float trb = kb * kappa * alpha / nd;
+        const float ndb = -kb * kappa * alpha * tr / (nd * nd);
+        *abar = (double)(kb * kappa * tr / nd);
+        float devb[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) devb[k] = -kk * Yb[k] + ndb * dev[k] / nd;
+        const float trd = devb[0] + devb[4] + devb[8];
+        axpi3(devb, 1.f, trb - trd / 3.f, eb);
+    }
+    float Xb[9];
+    ls.adjoint(X, eb, Xb);
+    cg_adjoint(Ftr, Xb, Fb_tr);
+    return true;
+}
+
+// The Hencky stress adjoint in the series form (the same contract as
+// hencky_adjoint); false outside the series range or for det F <= 0, where
+// the caller takes the eigen form.
+__device__ bool hencky_adjoint_series(const float F[9], const float tb[9], float mu, float la, double dmu, double dla,
+                                      float Fb[9], double* e_part) {
+    float X[9];
+    if (!(cg_minus_i(F, X) <= ADJ_SERIES_MAX2)) return false;
+    const float J = F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) +
+                    F[2] * (F[3] * F[7] - F[4] * F[6]);
+    if (!(J > 0.f)) return false;
+    LogSeries ls;
+    float e[9];
+    ls.eval(X, e);
+    // tau = 2 mu eps + lambda tr(eps) I: epsbar = 2 mu taubar + lambda tr(taubar) I
+    const float trt = tb[0] + tb[4] + tb[8];
+    float eb[9];
+    axpi3(tb, 2.f * mu, la * trt, eb);
+    float Xb[9];
+    ls.adjoint(X, eb, Xb);
+    cg_adjoint(F, Xb, Fb);
+    double te = 0.0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) te += (double)tb[k] * (double)e[k];
+    *e_part = 2.0 * te * dmu + (double)trt * (double)(e[0] + e[4] + e[8]) * dla;
+    return true;
+}
+
 // d alpha / d phi (phi in degrees) for alpha = sqrt(2/3) 2 sin phi / (3 - sin phi).
 __device__ __forceinline__ double dalpha_dphi(double alpha) {
     const double k = 0.816496580927726 * 2.0;     // sqrt(2/3) * 2
@@ -408,7 +632,8 @@ __global__ void __launch_bounds__(128) k_adj_g2p(const float* __restrict__ ps, i
             }
         double abar = 0.0;
         const double alpha = (double)ps[PPHI * stride + p];
-        if (dp_map_adjoint(Ftr, alpha, kappa, Fb_n, Fbt, &abar)) {
+        if (dp_map_adjoint_series(Ftr, (float)alpha, (float)kappa, Fb_n, Fbt, &abar) ||
+            dp_map_adjoint(Ftr, alpha, kappa, Fb_n, Fbt, &abar)) {
 #pragma unroll
             for (int k = 0; k < 9; ++k) Fb_n[k] = Fbt[k];
             phi_part = abar * dalpha_dphi(alpha);
@@ -685,7 +910,8 @@ __global__ void __launch_bounds__(128) k_adj_p2g(const float* __restrict__ ps, i
             float Fbs[9];
 #pragma unroll
             for (int k = 0; k < 9; ++k) Fbs[k] = ac[AF + k];
-            e_part = hencky_adjoint(F, tb, (double)P.mu, (double)P.lambda, dmu_dE, dla_dE, Fbs);
+            if (!hencky_adjoint_series(F, tb, P.mu, P.lambda, dmu_dE, dla_dE, Fbs, &e_part))
+                e_part = hencky_adjoint(F, tb, (double)P.mu, (double)P.lambda, dmu_dE, dla_dE, Fbs);
 #pragma unroll
             for (int k = 0; k < 9; ++k) ac[AF + k] = Fbs[k];
         } else {

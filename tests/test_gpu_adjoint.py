@@ -11,8 +11,8 @@ from tests.helpers import oracle_for, small_blob
 pytestmark = pytest.mark.gpu
 
 
-def _blob(floor=False, dp=False):
-    wl, Cm, F = small_blob(n=2000, seed=21, E=1e5, vscale=0.5, cscale=2.0, fscale=0.03, dt=2e-4,
+def _blob(floor=False, dp=False, fscale=0.03):
+    wl, Cm, F = small_blob(n=2000, seed=21, E=1e5, vscale=0.5, cscale=2.0, fscale=fscale, dt=2e-4,
                            material=W.DRUCKER_PRAGER if dp else W.NEOHOOKEAN)
     if dp:
         # per-particle friction angles (degrees)
@@ -42,10 +42,13 @@ def _pick(x, h, rng, k):
     return rng.choice(np.flatnonzero(ok), k, replace=False)
 
 
-@pytest.mark.parametrize("floor,dp", [(False, False), (True, False), (False, True), (True, True)])
-def test_one_step_adjoint_matches_fp64_differences(oracle_mod, floor, dp):
+# fscale 0.03 puts most particles' ||F F^T - I|| above 1/16 (the return map and
+# Hencky stress adjoints through the FP64 SVD), 0.005 below it (their series forms)
+@pytest.mark.parametrize("floor,dp,fscale", [(False, False, 0.03), (True, False, 0.03), (False, True, 0.03),
+                                             (True, True, 0.03), (False, True, 0.005), (True, True, 0.005)])
+def test_one_step_adjoint_matches_fp64_differences(oracle_mod, floor, dp, fscale):
     import torch
-    wl, Cm, F = _blob(floor, dp)
+    wl, Cm, F = _blob(floor, dp, fscale)
     n = wl.n
     rng = np.random.default_rng(5)
     wts = (rng.standard_normal((n, 3)), rng.standard_normal((n, 3)), rng.standard_normal((n, 9)) * 1e-2,
