@@ -90,6 +90,47 @@ def measured_traffic(workload: str, kernel: str):
     return None
 
 
+def measured_flops_per_particle(kernel: str):
+    """FP32 operations per particle of a transfer kernel from the committed ncu
+    capture of the 1M column (profiles/flops.txt), or None when the kernel
+    source changed after the counters were taken."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2605_28525_b300", "csrc", "transfer.cu")
+    try:
+        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+        for line in open(os.path.join(ROOT, "profiles", "flops.txt")):
+            f = line.split()
+            if len(f) == 4 and not line.startswith("#") and f[0] == "column_collapse_1M" and f[1] == kernel \
+                    and f[3] == sha:
+                return int(f[2]) / 1048576.0
+    except OSError:
+        pass
+    return None
+
+
+def alu_check(wl, phases: dict, sm_mhz):
+    """FP32 rate of P2G and G2P against the FFMA peak at the sampled SM clock
+    (148 SMs x 128 lanes x 2 flop per cycle): the ALU cross-check beside the
+    HBM roofline.  The operation counts are the Drucker-Prager column's, so
+    other materials get none."""
+    from paper_2605_28525_b300 import workloads as W
+    if not sm_mhz or wl.material != W.DRUCKER_PRAGER:
+        return None
+    n = wl.n
+    peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    out = {"peak_tflops": peak, "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x median SM clock",
+           "flop_source": "per-particle FP32 operation count of the 1M Drucker-Prager column's ncu capture "
+                          "(profiles/flops.txt)"}
+    for k in ("p2g", "g2p"):
+        f = measured_flops_per_particle(k)
+        if f is None:
+            out[k] = None
+            continue
+        tf = f * n / (phases[k] * 1e-3) / 1e12
+        out[k] = {"flop_per_particle": f, "achieved_tflops": tf, "frac": tf / peak}
+    return out
+
+
 def make_workload(name: str):
     from paper_2605_28525_b300 import workloads as W
     if name == "column_collapse_1M":
@@ -551,6 +592,7 @@ def main():
                          "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                          "alg_bytes_per_launch": alg_bytes, "kernel_ms": phases[dom]},
             "phases_ms": phases,
+            "alu_check": alu_check(wl, phases, (clk.summary() or {}).get("sm_mhz")),
             "cpu_baseline": cpu,
             "e2e": e2e,
             "dense_gpu": dense,
