@@ -50,7 +50,8 @@ struct DevStatus {
     unsigned int gen;            // step generation (block "holds particles" marks)
     unsigned int go;             // the running step's insert may proceed (written by the table clear)
     unsigned int work;           // next P2G work unit (dynamic scheduling; zeroed by the table clear)
-    unsigned int pad[5];
+    unsigned int scan_done[2];   // tile-scan arrival counters (bit-mask scan, bin scan); left at 0
+    unsigned int pad[3];
 };
 
 __device__ __forceinline__ void raise_flag(DevStatus* s, unsigned int* word, unsigned int bits) {

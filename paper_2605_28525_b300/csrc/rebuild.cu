@@ -576,17 +576,61 @@ __global__ void __launch_bounds__(256) k_particle_bins(int64_t n, const uint32_t
 
 constexpr int SC_THREADS = 256, SC_ITEMS = 8, SC_TILE = SC_THREADS * SC_ITEMS;
 
+// The end of a tile scan: every CTA has written its tile total to tsum; the
+// last CTA to arrive (counted on `counter`, which it resets) turns the
+// totals into exclusive tile offsets and writes the grand total to
+// tsum[ntiles].  Every thread of every CTA calls it.
+__device__ __forceinline__ void finish_tile_sums(int* __restrict__ tsum, int ntiles, unsigned int* counter) {
+    __shared__ int wsum[SC_THREADS / 32];
+    __shared__ int carry;
+    __shared__ bool last;
+    __threadfence();   // this CTA's total is visible device-wide before the CTA counts in
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1u;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int b = 0; b < ntiles; b += SC_THREADS) {
+        const int i = b + threadIdx.x;
+        const int v = i < ntiles ? __ldcg(&tsum[i]) : 0;   // other CTAs' totals: from L2
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        int pre = 0;
+        for (int k = 0; k < w; ++k) pre += wsum[k];
+        const int excl = carry + pre + x - v;
+        __syncthreads();
+        if (i < ntiles) tsum[i] = excl;
+        if (threadIdx.x == SC_THREADS - 1) carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        tsum[ntiles] = carry;
+        *counter = 0u;
+    }
+}
+
 // Exclusive scan of the live bins (live blocks x B3; the grid covers the
-// capacity), step 1: each tile of 2048 bins scanned locally; tile totals
-// (zero for tiles past the live bins).
+// capacity), steps 1 and 2: each tile of 2048 bins scanned locally, tile
+// totals (zero for tiles past the live bins) turned into tile offsets by the
+// last CTA.
 __global__ void __launch_bounds__(SC_THREADS) k_scan_tiles(const int* __restrict__ in, int64_t cap, int B3,
-                                                           const DevStatus* st, int* __restrict__ out,
+                                                           DevStatus* st, int* __restrict__ out,
                                                            int* __restrict__ tsum) {
     __shared__ int wsum[SC_THREADS / 32];
     if (cta_aborted(st)) return;
     const int64_t n = live_blocks(st, cap) * B3;
     if ((int64_t)blockIdx.x * SC_TILE >= n) {
         if (threadIdx.x == 0) tsum[blockIdx.x] = 0;
+        finish_tile_sums(tsum, (int)gridDim.x, &st->scan_done[1]);
         return;
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -615,36 +659,7 @@ __global__ void __launch_bounds__(SC_THREADS) k_scan_tiles(const int* __restrict
         run += v[j];
     }
     if (threadIdx.x == SC_THREADS - 1) tsum[blockIdx.x] = pre + x;
-}
-
-// Step 2: exclusive scan of the tile totals (one CTA); tsum[ntiles] = total.
-__global__ void __launch_bounds__(1024) k_scan_sums(int* __restrict__ tsum, int ntiles, const DevStatus* st) {
-    __shared__ int wsum[32];
-    __shared__ int carry;
-    if (cta_aborted(st)) return;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int b = 0; b < ntiles; b += 1024) {
-        const int i = b + threadIdx.x;
-        const int v = i < ntiles ? tsum[i] : 0;
-        int x = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) wsum[w] = x;
-        __syncthreads();
-        int pre = 0;
-        for (int k = 0; k < w; ++k) pre += wsum[k];
-        const int excl = carry + pre + x - v;
-        __syncthreads();
-        if (i < ntiles) tsum[i] = excl;
-        if (threadIdx.x == 1023) carry = excl + v;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) tsum[ntiles] = carry;
+    finish_tile_sums(tsum, (int)gridDim.x, &st->scan_done[1]);
 }
 
 // Step 3: add the tile offsets; cs[n] = total.
@@ -657,10 +672,10 @@ __global__ void k_scan_add(int* __restrict__ cs, int64_t cap, int B3, const DevS
     if (i == n) cs[n] = tsum[ntiles];
 }
 
-// Exclusive scan of the bit counts of the block mask's words, step 1 (the
-// scan's steps 2 and 3 are k_scan_sums and k_scan_add_n).
+// Exclusive scan of the bit counts of the block mask's words, steps 1 and 2
+// (step 3 is k_scan_add_n).
 __global__ void __launch_bounds__(SC_THREADS) k_bits_scan_tiles(const uint32_t* __restrict__ bmask, int64_t n,
-                                                                const DevStatus* st, int* __restrict__ out,
+                                                                DevStatus* st, int* __restrict__ out,
                                                                 int* __restrict__ tsum) {
     __shared__ int wsum[SC_THREADS / 32];
     if (cta_aborted(st)) return;
@@ -690,6 +705,7 @@ __global__ void __launch_bounds__(SC_THREADS) k_bits_scan_tiles(const uint32_t* 
         run += v[j];
     }
     if (threadIdx.x == SC_THREADS - 1) tsum[blockIdx.x] = pre + x;
+    finish_tile_sums(tsum, (int)gridDim.x, &st->scan_done[0]);
 }
 
 // Step 3 for a fixed count n: add the tile offsets; cs[n] = total.
@@ -782,10 +798,9 @@ cudaError_t launch_insert(mpm_ctx* c, int64_t ins_cap) {
     if (c->scan) {   // Alg. 3: the scan of the marks gives the block count before the host reads it
         const int ntiles = (int)((c->bwords + SC_TILE - 1) / SC_TILE);
         k_bits_scan_tiles<<<ntiles, SC_THREADS, 0, c->ls>>>(c->bmask, c->bwords, c->dstat, c->bpre, c->btsum);
-        k_scan_sums<<<1, 1024, 0, c->ls>>>(c->btsum, ntiles, c->dstat);
         k_scan_add_n<<<blocks_for(c->bwords + 1, 256), 256, 0, c->ls>>>(c->bpre, c->bwords, c->dstat, c->btsum, ntiles);
         k_scan_count<<<1, 1, 0, c->ls>>>(c->bpre, c->bwords, ins_cap, c->dstat);
-        c->launches += 4;
+        c->launches += 3;
     }
     return cudaGetLastError();
 }
@@ -821,12 +836,11 @@ cudaError_t launch_assign(mpm_ctx* c) {
     } else if (c->bmask) {
         const int ntiles = (int)((c->bwords + SC_TILE - 1) / SC_TILE);
         k_bits_scan_tiles<<<ntiles, SC_THREADS, 0, c->ls>>>(c->bmask, c->bwords, c->dstat, c->bpre, c->btsum);
-        k_scan_sums<<<1, 1024, 0, c->ls>>>(c->btsum, ntiles, c->dstat);
         k_scan_add_n<<<blocks_for(c->bwords + 1, 256), 256, 0, c->ls>>>(c->bpre, c->bwords, c->dstat, c->btsum, ntiles);
         k_assign_bits<<<blocks_for(cap * c->B3, 256), 256, 0, c->ls>>>(c->akey[0], c->aslot[0], cap, c->dstat, c->P,
                                                                        c->bmask, c->bpre, c->hvals, c->bcoord, c->gmv,
                                                                        c->gf, bins, c->B3, zero);
-        c->launches += 4;
+        c->launches += 3;
     } else {
         const int bits = 64 - __builtin_clzll((unsigned long long)(c->n_dom_blocks > 1 ? c->n_dom_blocks - 1 : 1));
         int sel = radix_sort_pairs(c, c->akey, c->aslot, cap, &c->dstat->n_active, bits, c->ls, &c->dstat->abort);
@@ -857,11 +871,10 @@ cudaError_t launch_particle_keys(mpm_ctx* c) {
                                                                   c->prank, c->dstat);
         const int ntiles = (int)((nkeys + SC_TILE - 1) / SC_TILE);
         k_scan_tiles<<<ntiles, SC_THREADS, 0, c->ls>>>(c->bins, cap, c->B3, c->dstat, c->cs, c->tsum);
-        k_scan_sums<<<1, 1024, 0, c->ls>>>(c->tsum, ntiles, c->dstat);
         k_scan_add<<<blocks_for(nkeys + 1, 256), 256, 0, c->ls>>>(c->cs, cap, c->B3, c->dstat, c->tsum, ntiles);
         k_bin_scatter<<<blocks_for(c->n, 512), 256, 0, c->ls>>>(c->n, c->pkey[0], c->prank, c->cs, c->pkey[1],
                                                                 c->pval[1], c->dstat);
-        c->launches += 5;
+        c->launches += 4;
         c->sorted_sel = 1;
         return cudaGetLastError();
     }

@@ -782,18 +782,11 @@ struct Neighbours {
 // neighbour table (L1-resident for the particles of one block).  The node
 // sums are factored over z: for each (a, b) the three z-nodes are first
 // reduced with w_z, dw_z and c w_z, then scattered into v_p, B_p and L_p.
-// THREADS x REGS: the CTA size and the registers a thread is compiled for
-// (at most REGS: 65536 / (THREADS x REGS) CTAs fit on an SM); the autotuner
-// picks one pair per context.
-// G2P of the particle at sorted position i (storage index p, block r).  With
-// STAGED its x, F, alpha and id come from a staging area (component k of
-// this thread at in[k * STG]: x 0-2, F 3-11, alpha 12, id 13), else from the
-// particle state.
-template <int B, bool DENSE, int MAT, bool STAGED, int STG>
+// G2P of the particle at sorted position i (storage index p, block r).
+template <int B, bool DENSE, int MAT>
 __device__ __forceinline__ void g2p_particle(const float* __restrict__ ps, float* __restrict__ po, int64_t stride,
                                              int64_t p, int64_t i, int r, const int* __restrict__ nbr,
-                                             const Params& P, const float4* __restrict__ gv, DevStatus* st,
-                                             const float* in) {
+                                             const Params& P, const float4* __restrict__ gv, DevStatus* st) {
     constexpr int NC = B * B * B;
     Neighbours<B, DENSE> nb;
     nb.load(P, nbr, r);
@@ -802,7 +795,7 @@ __device__ __forceinline__ void g2p_particle(const float* __restrict__ ps, float
     float xp[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        xp[a] = STAGED ? in[a * STG] : ps[(PX + a) * stride + p];
+        xp[a] = ps[(PX + a) * stride + p];
         const float fx = xp[a] * P.inv_h;
         const int bi = base_index(fx);
         d[a] = fx - (float)bi;
@@ -873,7 +866,7 @@ __device__ __forceinline__ void g2p_particle(const float* __restrict__ ps, float
     const float ls = P.dt * P.inv_h;
     float F[9], Fn[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) F[k] = STAGED ? in[(3 + k) * STG] : ps[(PF + k) * stride + p];
+    for (int k = 0; k < 9; ++k) F[k] = ps[(PF + k) * stride + p];
     const float L[9] = {Lx[0], Ly[0], Lz[0], Lx[1], Ly[1], Lz[1], Lx[2], Ly[2], Lz[2]};
 #pragma unroll
     for (int i2 = 0; i2 < 3; ++i2)
@@ -881,7 +874,7 @@ __device__ __forceinline__ void g2p_particle(const float* __restrict__ ps, float
         for (int j2 = 0; j2 < 3; ++j2)
             Fn[i2 * 3 + j2] = F[i2 * 3 + j2] + ls * (L[i2 * 3 + 0] * F[0 * 3 + j2] + L[i2 * 3 + 1] * F[1 * 3 + j2] +
                                                     L[i2 * 3 + 2] * F[2 * 3 + j2]);
-    const float alpha = STAGED ? in[12 * STG] : ps[PPHI * stride + p];
+    const float alpha = ps[PPHI * stride + p];
     Sym tau;
     bool ok;
     if (MAT == MPM_NEOHOOKEAN) ok = nh_tau(P, Fn, tau);
@@ -914,9 +907,12 @@ __device__ __forceinline__ void g2p_particle(const float* __restrict__ ps, float
     po[(PT + 4) * stride + i] = tau.yz;
     po[(PT + 5) * stride + i] = tau.zz;
     po[PPHI * stride + i] = alpha;
-    po[PID * stride + i] = STAGED ? in[13 * STG] : ps[PID * stride + p];
+    po[PID * stride + i] = ps[PID * stride + p];
 }
 
+// THREADS x REGS: the CTA size and the registers a thread is compiled for
+// (at most REGS: 65536 / (THREADS x REGS) CTAs fit on an SM); the autotuner
+// picks one pair per context.
 template <int B, bool DENSE, int MAT, int THREADS, int REGS>
 __global__ void __launch_bounds__(THREADS, 65536 / (THREADS * REGS)) k_g2p(const float* __restrict__ ps, float* __restrict__ po, int64_t stride,
                                               const uint32_t* __restrict__ perm, const uint32_t* __restrict__ skey,
@@ -926,7 +922,7 @@ __global__ void __launch_bounds__(THREADS, 65536 / (THREADS * REGS)) k_g2p(const
     if (cta_aborted(st)) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    g2p_particle<B, DENSE, MAT, false, 1>(ps, po, stride, perm[i], i, (int)(skey[i] >> S3), nbr, P, gv, st, nullptr);
+    g2p_particle<B, DENSE, MAT>(ps, po, stride, perm[i], i, (int)(skey[i] >> S3), nbr, P, gv, st);
 }
 
 
