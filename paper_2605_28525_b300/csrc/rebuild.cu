@@ -426,14 +426,21 @@ __device__ __forceinline__ int first_geq(const uint32_t* __restrict__ skey, int 
 }
 
 // Reorders every block's particles from (cell, k) to k-major order: the
-// k-th particle of each cell (cells in l order) before any (k+1)-th one, and
-// records the particle count per cell.  One warp per block; lane l handles
-// cells l and l + 32.  Output goes to the spare sort buffers.
+// k-th particle of each cell (cells in slot order) before any (k+1)-th one,
+// and records the particle count per slot.  One warp per block; lane l
+// handles slots l and l + 32.  Without `cperm` slot j is cell j.  With it
+// (the fast mode) the slots hold the block's cells by particle count,
+// largest first (ties by cell index), and cperm records the cell of every
+// slot: P2G's two work units of a block are slots 0-31 and 32-63, and a unit
+// takes as many rounds as its fullest cell, so the heavy cells share a unit.
+// Output goes to the spare sort buffers.
 __global__ void __launch_bounds__(128) k_interleave(const uint32_t* __restrict__ skey, const uint32_t* __restrict__ perm,
                                                     const int* __restrict__ bstart, const int* __restrict__ bend,
                                                     const int* __restrict__ pblocks, const DevStatus* stc,
                                                     const int* __restrict__ cs, uint32_t* __restrict__ skey2,
-                                                    uint32_t* __restrict__ perm2, int* __restrict__ ccount) {
+                                                    uint32_t* __restrict__ perm2, int* __restrict__ ccount,
+                                                    uint8_t* __restrict__ cperm) {
+    __shared__ unsigned char slot_cell[4][64];
     if (cta_aborted(stc)) return;
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * 4 + (threadIdx.x >> 5), nw = gridDim.x * 4;
@@ -455,7 +462,37 @@ __global__ void __launch_bounds__(128) k_interleave(const uint32_t* __restrict__
             lo1 = first_geq(skey, s, e, base + 32 + lane);
             hi1 = first_geq(skey, lo1, e, base + 33 + lane);
         }
-        const int cnt0 = hi0 - lo0, cnt1 = hi1 - lo1;
+        int cnt0 = hi0 - lo0, cnt1 = hi1 - lo1;
+        int cell0 = lane, cell1 = lane + 32;
+        if (cperm) {
+            // slot of cell c = the cells with more particles, or as many and a
+            // smaller index (a permutation of 0..63)
+            int q0 = 0, q1 = 0;
+            for (int j = 0; j < 32; ++j) {
+                const int a = __shfl_sync(FULL, cnt0, j), b = __shfl_sync(FULL, cnt1, j);   // cells j, j + 32
+                q0 += (a > cnt0 || (a == cnt0 && j < lane)) + (b > cnt0);
+                q1 += (a >= cnt1) + (b > cnt1 || (b == cnt1 && j < lane));
+            }
+            unsigned char* sc = slot_cell[threadIdx.x >> 5];
+            sc[q0] = (unsigned char)lane;
+            sc[q1] = (unsigned char)(lane + 32);
+            __syncwarp();
+            cell0 = sc[lane];
+            cell1 = sc[lane + 32];
+            __syncwarp();   // the slots are read before the next block rewrites them
+            // range of the cells now in slots lane and lane + 32 (cell c's range
+            // sits in lane c & 31, in its first pair for c < 32)
+            const int l0a = __shfl_sync(FULL, lo0, cell0 & 31), l0b = __shfl_sync(FULL, lo1, cell0 & 31);
+            const int c0a = __shfl_sync(FULL, cnt0, cell0 & 31), c0b = __shfl_sync(FULL, cnt1, cell0 & 31);
+            const int l1a = __shfl_sync(FULL, lo0, cell1 & 31), l1b = __shfl_sync(FULL, lo1, cell1 & 31);
+            const int c1a = __shfl_sync(FULL, cnt0, cell1 & 31), c1b = __shfl_sync(FULL, cnt1, cell1 & 31);
+            lo0 = cell0 < 32 ? l0a : l0b;
+            lo1 = cell1 < 32 ? l1a : l1b;
+            cnt0 = cell0 < 32 ? c0a : c0b;
+            cnt1 = cell1 < 32 ? c1a : c1b;
+            cperm[(int64_t)r * 64 + lane] = (uint8_t)cell0;
+            cperm[(int64_t)r * 64 + 32 + lane] = (uint8_t)cell1;
+        }
         ccount[(int64_t)r * 64 + lane] = cnt0;
         ccount[(int64_t)r * 64 + 32 + lane] = cnt1;
         int off = 0;
@@ -465,12 +502,12 @@ __global__ void __launch_bounds__(128) k_interleave(const uint32_t* __restrict__
             if (cnt0 > k) {
                 const int pos = s + off + __popc(M0 & lt);
                 perm2[pos] = perm[lo0 + k];
-                skey2[pos] = base + lane;
+                skey2[pos] = base + cell0;
             }
             if (cnt1 > k) {
                 const int pos = s + off + __popc(M0) + __popc(M1 & lt);
                 perm2[pos] = perm[lo1 + k];
-                skey2[pos] = base + 32 + lane;
+                skey2[pos] = base + cell1;
             }
             off += __popc(M0) + __popc(M1);
         }
@@ -908,7 +945,8 @@ cudaError_t launch_ranges(mpm_ctx* c, const uint32_t* skey) {
     if (c->B == 4) {
         const int o = 1 - c->sorted_sel;
         k_interleave<<<148 * 8, 128, 0, c->ls>>>(skey, c->pval[c->sorted_sel], c->bstart, c->bend, c->pblocks, c->dstat,
-                                                cnt ? c->cs : nullptr, c->pkey[o], c->pval[o], c->ccount);
+                                                cnt ? c->cs : nullptr, c->pkey[o], c->pval[o], c->ccount,
+                                                cnt ? c->cperm : nullptr);
         c->sorted_sel = o;
         ++c->launches;
     }

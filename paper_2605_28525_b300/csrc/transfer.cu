@@ -150,14 +150,19 @@ template <bool DENSE, bool DET>
 __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, MPM_P2G_MINB) k_p2g_cells(
     const float* __restrict__ ps, int64_t stride, const uint32_t* __restrict__ perm,
     const int* __restrict__ bstart, const int* __restrict__ bend, const int* __restrict__ pblocks,
-    const int* __restrict__ ccount, const DevStatus* __restrict__ stc, Params P, const int* __restrict__ nbr,
-    float4* __restrict__ gmv, float4* __restrict__ gf, float* __restrict__ tbuf, DevStatus* st) {
+    const int* __restrict__ ccount, const uint8_t* __restrict__ cperm, const DevStatus* __restrict__ stc, Params P,
+    const int* __restrict__ nbr, float4* __restrict__ gmv, float4* __restrict__ gf, float* __restrict__ tbuf,
+    DevStatus* st) {
     using K = CellTileCfg;
-    // Work unit: a half block (32 cells, tile z-layers 2h..2h+3) in the fast
-    // mode, a whole block in the deterministic mode (its tile goes to tbuf as
-    // one piece).  Units are handed out dynamically.
+    // Work unit: half a block's cells in the fast mode, a whole block in the
+    // deterministic mode (its tile goes to tbuf as one piece).  Units are
+    // handed out dynamically.  Slot j (lane j % 32 of half j / 32) holds
+    // cell cperm[j] when the rebuild ordered the cells by count (the fast
+    // mode on the sparse grid: the units span the whole tile), else cell j
+    // (a half is then the z-layers 2h, 2h+1 and its tile layers 2h..2h+3).
     constexpr int HU = DET ? 1 : 2;
-    constexpr int TZ = DET ? K::T : 4;
+    const bool by_count = !DET && cperm != nullptr;
+    const int TZ = (DET || by_count) ? K::T : 4;
     __shared__ float tiles[K::WARPS][7][K::TILE];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     float(&tile)[7][K::TILE] = tiles[wid];
@@ -175,14 +180,15 @@ __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, MPM_P2G_MINB) k_p2g_c
         if (u >= nunits) break;
         const int r = pblocks[u / HU];
         const int h0 = DET ? 0 : u % HU, h1 = DET ? 2 : h0 + 1;
-        const int zoff = DET ? 0 : 2 * h0;              // block z-layer of the tile's layer 0
+        const int zoff = (DET || by_count) ? 0 : 2 * h0;   // block z-layer of the tile's layer 0
         const int s = bstart[r], kcap = bend[r] - s;   // no cell holds more than the block's particles
         const int cnt0 = ccount[(int64_t)r * 64 + lane], cnt1 = ccount[(int64_t)r * 64 + 32 + lane];
         if (!DET && __ballot_sync(FULL, (h0 ? cnt1 : cnt0) > 0) == 0u) continue;   // empty half
 #pragma unroll 1
         for (int h = h0; h < h1; ++h) {
             const int cnt = h ? cnt1 : cnt0;
-            const int cx = lane & 3, cy = (lane >> 2) & 3, cz = 2 * h + (lane >> 4) - zoff;
+            const int cell = by_count ? (int)cperm[(int64_t)r * 64 + 32 * h + lane] : 32 * h + lane;
+            const int cx = cell & 3, cy = (cell >> 2) & 3, cz = (cell >> 4) - zoff;
 #if MPM_P2G_PCACHE
             // storage indices of this lane's first rounds, loaded once for the
             // three x-offset passes (one dependent load less per round)
@@ -968,9 +974,10 @@ cudaError_t launch_p2g(mpm_ctx* c) {
         ++c->launches;
         return cudaGetLastError();
     }
+    const uint8_t* cp = counting_sort(c) ? c->cperm : nullptr;   // cells ordered by count (fast sparse mode)
 #define MPM_CELLS(D_, T_)                                                                                         \
     k_p2g_cells<D_, T_><<<NUM_SMS * c->tune.p2g_ctas_per_sm, CellTileCfg::WARPS * 32, 0, c->ls>>>(ps, c->pstride, perm, c->bstart, c->bend, \
-                                                                       c->pblocks, c->ccount, c->dstat, c->P,   \
+                                                                       c->pblocks, c->ccount, cp, c->dstat, c->P, \
                                                                        c->nbr, c->gmv, c->gf, c->tbuf, c->dstat)
     if (c->dense) {
         if (c->det) MPM_CELLS(true, true);
