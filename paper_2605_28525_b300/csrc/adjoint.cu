@@ -347,7 +347,7 @@ __device__ double hencky_adjoint(const float Ff[9], const float tb[9], double mu
 // no divided difference of singular values to lose precision in.  Matrices
 // are full 3x3, row-major.
 
-constexpr float ADJ_SERIES_MAX2 = 0.0625f * 0.0625f;   // the forward's threshold, squared
+constexpr float ADJ_SERIES_MAX2 = MPM_SERIES_MAX * MPM_SERIES_MAX;   // the forward's threshold, squared
 
 __device__ __forceinline__ void mm3(const float A[9], const float B[9], float C[9]) {   // C = A B
 #pragma unroll

@@ -189,6 +189,12 @@ __device__ __forceinline__ int lookup_block(const Params& P, const HashView& hv,
     return hash_find(hv, pack_key(bi, bj, bk), P.max_probe);
 }
 
+// ||F F^T - I||_F up to which the Drucker-Prager return map and the Hencky
+// stress take their power-series form (forward and adjoint alike).
+#ifndef MPM_SERIES_MAX
+#define MPM_SERIES_MAX 0.0625f
+#endif
+
 // ---------------------------------------------------- quadratic B-spline
 
 // Cell/base index: floor(x/h - 1/2).  x/h is exact for power-of-two h and the

@@ -60,13 +60,14 @@ __device__ __forceinline__ int block_rank(const Params& P, const HashView& hv, i
 // ------------------------------------------------------- P2G: cell lanes
 
 // Particles of a block are stored "k-major": the k-th particle of every cell
-// (cells in l order) before the (k+1)-th particle of any cell; ccount holds
-// the particles per cell.  One warp owns one block and a private tile of
-// (B+2)^3 = 216 nodes; lane l owns cell h*32 + l of half h (cz in {2h, 2h+1}).
-// For each (half, x-offset a) pass the lanes walk k = 0, 1, ...: the k-th
-// particles of the 32 cells are consecutive in memory (coalesced loads), and
-// each lane accumulates its particle's 9 nodes (a, 0..2, 0..2) x 7 channels
-// in registers.  At the end of a pass the lanes hold distinct cells and the
+// (cells in slot order) before the (k+1)-th particle of any cell; ccount
+// holds the particles per slot.  A warp takes a work unit of 32 slots (lane
+// l owns slot 32h + l of unit h; the rebuild orders the slots by count in the
+// fast sparse mode) with a private tile of (B+2)^3 = 216 nodes.  For each
+// (unit, x-offset a) pass the lanes walk k = 0, 1, ...: the k-th particles of
+// the 32 cells are consecutive in memory (coalesced loads), and each lane
+// accumulates its particle's 9 nodes (a, 0..2, 0..2) x 7 channels in
+// registers.  At the end of a pass the lanes hold distinct cells and the
 // same a, so for each node offset (b, c) their target nodes are distinct:
 // the tile is updated with plain read-modify-write, one warp-synchronised
 // step per offset, no atomics.  The finished tile is added to the active
@@ -143,7 +144,7 @@ __device__ __forceinline__ void p2g_accumulate(const Params& P, const P2GIn& in,
 }
 
 #ifndef MPM_P2G_PCACHE
-#define MPM_P2G_PCACHE 8   // rounds whose particle indices a lane loads once per half block
+#define MPM_P2G_PCACHE 8   // rounds whose particle indices a lane loads once per work unit
 #endif
 
 template <bool DENSE, bool DET>
@@ -642,10 +643,6 @@ __device__ __forceinline__ bool dp_update_eig(const Params& P, float alpha, floa
 // on the cone and -eps at its tip.  When X = b - I is small, ln(I + X) and
 // exp come from their power series, with products of symmetric matrices that
 // commute (polynomials in X); larger stretches take the Jacobi path above.
-
-#ifndef MPM_SERIES_MAX
-#define MPM_SERIES_MAX 0.0625f   // ||F F^T - I||_F up to which the series path is taken
-#endif
 
 // A B for symmetric A and B that commute: the product is symmetric.
 __device__ __forceinline__ Sym sym_mul(const Sym& a, const Sym& b) {
