@@ -441,6 +441,7 @@ __global__ void __launch_bounds__(128) k_interleave(const uint32_t* __restrict__
                                                     uint32_t* __restrict__ perm2, int* __restrict__ ccount,
                                                     uint8_t* __restrict__ cperm) {
     __shared__ unsigned char slot_cell[4][64];
+    __shared__ int hist_all[4][64], hist_low[4][64];
     if (cta_aborted(stc)) return;
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * 4 + (threadIdx.x >> 5), nw = gridDim.x * 4;
@@ -466,14 +467,38 @@ __global__ void __launch_bounds__(128) k_interleave(const uint32_t* __restrict__
         int cell0 = lane, cell1 = lane + 32;
         if (cperm) {
             // slot of cell c = the cells with more particles, or as many and a
-            // smaller index (a permutation of 0..63)
-            int q0 = 0, q1 = 0;
-            for (int j = 0; j < 32; ++j) {
-                const int a = __shfl_sync(FULL, cnt0, j), b = __shfl_sync(FULL, cnt1, j);   // cells j, j + 32
-                q0 += (a > cnt0 || (a == cnt0 && j < lane)) + (b > cnt0);
-                q1 += (a >= cnt1) + (b > cnt1 || (b == cnt1 && j < lane));
+            // smaller index (a permutation of 0..63); counts are compared
+            // clamped to 63, which only reorders cells fuller than that
+            const int w = threadIdx.x >> 5;
+            const int v0 = min(cnt0, 63), v1 = min(cnt1, 63);
+            int* hall = hist_all[w];
+            int* hlow = hist_low[w];
+            hall[lane] = hall[lane + 32] = 0;
+            hlow[lane] = hlow[lane + 32] = 0;
+            __syncwarp();
+            atomicAdd(&hall[v0], 1);
+            atomicAdd(&hall[v1], 1);
+            atomicAdd(&hlow[v0], 1);   // cells 0-31 only
+            __syncwarp();
+            // more[v] = cells with a clamped count above v (a suffix sum)
+            const int h0 = hall[lane], h1 = hall[lane + 32];
+            int s1 = h1, s0 = h0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {   // inclusive suffix sums inside each half
+                const int t1 = __shfl_down_sync(FULL, s1, o), t0 = __shfl_down_sync(FULL, s0, o);
+                if (lane + o < 32) {
+                    s1 += t1;
+                    s0 += t0;
+                }
             }
-            unsigned char* sc = slot_cell[threadIdx.x >> 5];
+            s0 += __shfl_sync(FULL, s1, 0);   // the upper half lies above every lower value
+            const int more0 = s0 - h0, more1 = s1 - h1;   // for values lane and lane + 32
+            const int m0a = __shfl_sync(FULL, more0, v0 & 31), m0b = __shfl_sync(FULL, more1, v0 & 31);
+            const int m1a = __shfl_sync(FULL, more0, v1 & 31), m1b = __shfl_sync(FULL, more1, v1 & 31);
+            const unsigned below = (1u << lane) - 1u;
+            const int q0 = (v0 < 32 ? m0a : m0b) + __popc(__match_any_sync(FULL, v0) & below);
+            const int q1 = (v1 < 32 ? m1a : m1b) + hlow[v1] + __popc(__match_any_sync(FULL, v1) & below);
+            unsigned char* sc = slot_cell[w];
             sc[q0] = (unsigned char)lane;
             sc[q1] = (unsigned char)(lane + 32);
             __syncwarp();
