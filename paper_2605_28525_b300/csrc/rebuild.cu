@@ -209,9 +209,14 @@ __device__ __forceinline__ void insert_particle(const float* __restrict__ ps, in
     }
 }
 
-// Each warp takes 64 consecutive particles, p and p + 32 per lane; both
-// particles' coordinates are loaded before the first one's probes, so the
-// second load overlaps them.
+#ifndef MPM_INSERT_PER_LANE
+#define MPM_INSERT_PER_LANE 2
+#endif
+constexpr int INS_PL = MPM_INSERT_PER_LANE;   // particles per lane in the insert
+
+// Each warp takes 32 x INS_PL consecutive particles, p, p + 32, ... per
+// lane; all their coordinates are loaded before the first one's probes, so
+// the later loads overlap them.
 template <int B, bool SCAN>
 __global__ void __launch_bounds__(256) k_insert(const float* __restrict__ ps, int64_t stride, int64_t n,
                                                 Params P, HashView hv, uint32_t* __restrict__ akey,
@@ -220,15 +225,15 @@ __global__ void __launch_bounds__(256) k_insert(const float* __restrict__ ps, in
                                                 DevStatus* st) {
     if (st->go == 0u) return;   // written by the clear before this kernel: uniform
     const int lane = threadIdx.x & 31;
-    const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * 2 + lane, p1 = p0 + 32;
-    float x0[3] = {0.f, 0.f, 0.f}, x1[3] = {0.f, 0.f, 0.f};
+    const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * INS_PL + lane;
+    float xs[INS_PL][3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        if (p0 < n) x0[a] = ps[(PX + a) * stride + p0];
-        if (p1 < n) x1[a] = ps[(PX + a) * stride + p1];
-    }
-    insert_particle<B, SCAN>(ps, stride, n, p0, x0, P, hv, akey, aslot, cap, bmask, pcode, st);
-    insert_particle<B, SCAN>(ps, stride, n, p1, x1, P, hv, akey, aslot, cap, bmask, pcode, st);
+    for (int h = 0; h < INS_PL; ++h)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) xs[h][a] = (p0 + 32 * h < n) ? ps[(PX + a) * stride + p0 + 32 * h] : 0.f;
+#pragma unroll
+    for (int h = 0; h < INS_PL; ++h)
+        insert_particle<B, SCAN>(ps, stride, n, p0 + 32 * h, xs[h], P, hv, akey, aslot, cap, bmask, pcode, st);
 }
 
 // Dense comparator: the identity map.  The particle's sort key is the block's
@@ -779,26 +784,33 @@ __global__ void k_scan_add_n(int* __restrict__ cs, int64_t n, const DevStatus* s
     if (i == n) cs[n] = tsum[ntiles];
 }
 
-// Scatter into (block, cell) order, two particles per thread (p and p + 32
-// within the warp's 64) for two load chains in flight.
+#ifndef MPM_SCATTER_PER_LANE
+#define MPM_SCATTER_PER_LANE 2
+#endif
+constexpr int SCT_PL = MPM_SCATTER_PER_LANE;   // particles per lane in the scatter
+
+// Scatter into (block, cell) order, SCT_PL particles per lane (p, p + 32,
+// ... within the warp's 32 x SCT_PL) for as many load chains in flight.
 __global__ void __launch_bounds__(256) k_bin_scatter(int64_t n, const uint32_t* __restrict__ key,
                                                      const uint32_t* __restrict__ prank, const int* __restrict__ cs,
                                                      uint32_t* __restrict__ skey, uint32_t* __restrict__ perm,
                                                      const DevStatus* st) {
     if (cta_aborted(st)) return;
     const int lane = threadIdx.x & 31;
-    const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * 2 + lane;
-    uint32_t k[2] = {0xffffffffu, 0xffffffffu}, r[2] = {0u, 0u};
+    const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * SCT_PL + lane;
+    uint32_t k[SCT_PL], r[SCT_PL];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < SCT_PL; ++h) {
         const int64_t p = p0 + 32 * h;
+        k[h] = 0xffffffffu;
+        r[h] = 0u;
         if (p < n) {
             k[h] = key[p];
             r[h] = prank[p];
         }
     }
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < SCT_PL; ++h) {
         if (k[h] == 0xffffffffu) continue;
         const int pos = cs[k[h]] + (int)r[h];
         skey[pos] = k[h];
@@ -847,7 +859,7 @@ cudaError_t launch_insert(mpm_ctx* c, int64_t ins_cap) {
     c->launches += 2;
     const float* ps = c->ps[c->cur];
 #define MPM_INS(B_, S_)                                                                                           \
-    k_insert<B_, S_><<<blocks_for(c->n, 512), 256, 0, c->ls>>>(ps, c->pstride, c->n, c->P, hv, c->akey[0],       \
+    k_insert<B_, S_><<<blocks_for(c->n, 256 * INS_PL), 256, 0, c->ls>>>(ps, c->pstride, c->n, c->P, hv, c->akey[0],       \
                                                                c->aslot[0], ins_cap, c->bmask, c->pcode, c->dstat)
     if (c->B == 4) {
         if (c->scan) MPM_INS(4, true);
@@ -934,7 +946,7 @@ cudaError_t launch_particle_keys(mpm_ctx* c) {
         const int ntiles = (int)((nkeys + SC_TILE - 1) / SC_TILE);
         k_scan_tiles<<<ntiles, SC_THREADS, 0, c->ls>>>(c->bins, cap, c->B3, c->dstat, c->cs, c->tsum);
         k_scan_add<<<blocks_for(nkeys + 1, 256), 256, 0, c->ls>>>(c->cs, cap, c->B3, c->dstat, c->tsum, ntiles);
-        k_bin_scatter<<<blocks_for(c->n, 512), 256, 0, c->ls>>>(c->n, c->pkey[0], c->prank, c->cs, c->pkey[1],
+        k_bin_scatter<<<blocks_for(c->n, 256 * SCT_PL), 256, 0, c->ls>>>(c->n, c->pkey[0], c->prank, c->cs, c->pkey[1],
                                                                 c->pval[1], c->dstat);
         c->launches += 4;
         c->sorted_sel = 1;
