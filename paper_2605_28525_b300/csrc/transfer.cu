@@ -864,9 +864,28 @@ __device__ __forceinline__ void g2p_particle(const float* __restrict__ ps, float
             }
         }
     }
-    // C = B D^-1 with B = h [Bx By Bz] and D = h^2/4 I; L = [Lx Ly Lz] / h
+    // C = B D^-1 with B = h [Bx By Bz] and D = h^2/4 I; L = [Lx Ly Lz] / h.
+    // x, v and C are written before the constitutive update, so that they
+    // hold no registers through it; one sum of every output tests them all
+    // for NaN or infinity.
     const float cs = 4.f * P.inv_h;
     const float ls = P.dt * P.inv_h;
+    float sum = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float xo = xp[a] + P.dt * vp[a];
+        sum += xo;
+        po[(PX + a) * stride + i] = xo;
+        po[(PV + a) * stride + i] = vp[a];
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float c0 = cs * Bx[k], c1 = cs * By[k], c2 = cs * Bz[k];
+        sum += c0 + c1 + c2;
+        po[(PC + 3 * k + 0) * stride + i] = c0;
+        po[(PC + 3 * k + 1) * stride + i] = c1;
+        po[(PC + 3 * k + 2) * stride + i] = c2;
+    }
     float F[9], Fn[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) F[k] = ps[(PF + k) * stride + p];
@@ -882,27 +901,13 @@ __device__ __forceinline__ void g2p_particle(const float* __restrict__ ps, float
     bool ok;
     if (MAT == MPM_NEOHOOKEAN) ok = nh_tau(P, Fn, tau);
     else ok = dp_update(P, alpha, Fn, tau);
-    float xo[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) xo[a] = xp[a] + P.dt * vp[a];
-    const float Cm[9] = {cs * Bx[0], cs * By[0], cs * Bz[0], cs * Bx[1], cs * By[1], cs * Bz[1],
-                         cs * Bx[2], cs * By[2], cs * Bz[2]};
-    // one test of a sum: a NaN or an infinity in any term makes it non-finite
-    float sum = xo[0] + xo[1] + xo[2] + tau.xx + tau.yy + tau.zz + tau.xy + tau.xz + tau.yz;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) sum += Fn[k] + Cm[k];
-    const bool fin = ok && isfinite(sum);
-    if (!fin) raise_flag(st, &st->numeric, 1u);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        po[(PX + a) * stride + i] = xo[a];
-        po[(PV + a) * stride + i] = vp[a];
-    }
+    sum += tau.xx + tau.yy + tau.zz + tau.xy + tau.xz + tau.yz;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-        po[(PC + k) * stride + i] = Cm[k];
+        sum += Fn[k];
         po[(PF + k) * stride + i] = Fn[k];
     }
+    if (!(ok && isfinite(sum))) raise_flag(st, &st->numeric, 1u);
     po[(PT + 0) * stride + i] = tau.xx;
     po[(PT + 1) * stride + i] = tau.xy;
     po[(PT + 2) * stride + i] = tau.xz;
