@@ -60,6 +60,35 @@ def test_p2g_parity_random_state(oracle_mod, material, B, flags):
     _check_p2g(o, wl, wl.x, wl.v, Cm, F, None, keys, nodes, g, B)
 
 
+@pytest.mark.parametrize("flags", [0, mpm.DETERMINISTIC])
+def test_p2g_parity_crowded_cells(oracle_mod, flags):
+    """Cells far fuller than the rest: one with 150 particles (above the 63 the
+    fast mode's count ordering distinguishes), one with 70, a few with 20, next
+    to sparse ones, so that the rounds run past the cached first eight and
+    most lanes of a unit idle in its late rounds."""
+    wl, Cm, F = small_blob(n=3000, seed=17, material=W.DRUCKER_PRAGER, E=1e7)
+    rng = np.random.default_rng(8)
+    h = wl.dx
+    x = wl.x.copy()
+    k = 0
+    for cell, cnt in (((14, 14, 14), 150), ((15, 14, 14), 70), ((12, 16, 13), 20), ((16, 12, 17), 20)):
+        c = np.asarray(cell, np.float64)
+        x[k:k + cnt] = ((c + 0.5 + rng.uniform(0.02, 0.98, (cnt, 3))) * h).astype(np.float32)
+        k += cnt
+    wl.x = x
+    o = oracle_for(wl)
+    sim = mpm.Simulation(mpm.config_from_workload(wl, flags=flags), wl.x, wl.v, Cm, F)
+    keys, nodes, g = _gpu_grid(sim, 4)
+    assert np.array_equal(keys, eq_keys(o.active_blocks(wl.x)))
+    _check_p2g(o, wl, wl.x, wl.v, Cm, F, None, keys, nodes, g, 4)
+    # a second step starts from the count-ordered, k-major particle order
+    sim.grid_update()
+    sim.g2p()
+    x1 = sim.read_particles()["x"]
+    sim.rebuild_active()
+    assert np.array_equal(sim.read_active(), eq_keys(o.active_blocks(x1)))
+
+
 def test_p2g_parity_per_particle_phi(oracle_mod):
     wl, Cm, F = small_blob(n=4000, seed=12, material=W.DRUCKER_PRAGER, E=1e7)
     phi = np.random.default_rng(2).uniform(25, 35, wl.n).astype(np.float32)
