@@ -101,7 +101,15 @@ struct P2GIn {
 
 // Adds one particle's contributions to the 9 nodes (a, 0..2, 0..2) of its
 // stencil: 7 channels (m, m v, f) per node, in units of m_p and -V0/h.
-__device__ __forceinline__ void p2g_accumulate(const Params& P, const P2GIn& in, int a, float (&acc)[3][3][7]) {
+// The 7 channels of one node, paired for Blackwell's packed FP32 pipes
+// (__ffma2_rn: two FMAs per instruction, each rounded as fmaf):
+// (m, m v_z), (m v_x, m v_y), (f_x, f_y), f_z.
+struct NodeAcc {
+    float2 m_mz, mxy, fxy;
+    float fz;
+};
+
+__device__ __forceinline__ void p2g_accumulate(const Params& P, const P2GIn& in, int a, NodeAcc (&acc)[3][3]) {
     float d[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
@@ -119,26 +127,27 @@ __device__ __forceinline__ void p2g_accumulate(const Params& P, const P2GIn& in,
     const float q0x = fmaf(hc[0], ox, in.v[0]) - hc[1] * d[1] - hc[2] * d[2];
     const float q0y = fmaf(hc[3], ox, in.v[1]) - hc[4] * d[1] - hc[5] * d[2];
     const float q0z = fmaf(hc[6], ox, in.v[2]) - hc[7] * d[1] - hc[8] * d[2];
+    const float2 hc25 = make_float2(hc[2], hc[5]);
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
         // tau . grad N over c: wz (tau_r0 dwx wy + tau_r1 wx dwy) + dwz tau_r2 wx wy
         const float Pw = wx * wy[b], Gx = dwx * wy[b], Gy = wx * dwy[b];
         const float A0 = t[0] * Gx + t[1] * Gy, A1 = t[1] * Gx + t[3] * Gy, A2 = t[2] * Gx + t[4] * Gy;
         const float B0 = t[2] * Pw, B1 = t[4] * Pw, B2 = t[5] * Pw;
-        const float qbx = fmaf(hc[1], (float)b, q0x), qby = fmaf(hc[4], (float)b, q0y),
-                    qbz = fmaf(hc[7], (float)b, q0z);
+        const float2 A01 = make_float2(A0, A1), B01 = make_float2(B0, B1);
+        const float2 qb = make_float2(fmaf(hc[1], (float)b, q0x), fmaf(hc[4], (float)b, q0y));
+        const float qbz = fmaf(hc[7], (float)b, q0z);
 #pragma unroll
         for (int cc = 0; cc < 3; ++cc) {
             const float N = Pw * wz[cc];
-            const float mx = fmaf(hc[2], (float)cc, qbx), my = fmaf(hc[5], (float)cc, qby),
-                        mz = fmaf(hc[8], (float)cc, qbz);
-            acc[b][cc][0] += N;
-            acc[b][cc][1] = fmaf(N, mx, acc[b][cc][1]);
-            acc[b][cc][2] = fmaf(N, my, acc[b][cc][2]);
-            acc[b][cc][3] = fmaf(N, mz, acc[b][cc][3]);
-            acc[b][cc][4] = fmaf(wz[cc], A0, fmaf(dwz[cc], B0, acc[b][cc][4]));
-            acc[b][cc][5] = fmaf(wz[cc], A1, fmaf(dwz[cc], B1, acc[b][cc][5]));
-            acc[b][cc][6] = fmaf(wz[cc], A2, fmaf(dwz[cc], B2, acc[b][cc][6]));
+            const float2 NN = make_float2(N, N);
+            const float2 mxy = __ffma2_rn(hc25, make_float2((float)cc, (float)cc), qb);
+            const float mz = fmaf(hc[8], (float)cc, qbz);
+            acc[b][cc].m_mz = __ffma2_rn(NN, make_float2(1.f, mz), acc[b][cc].m_mz);   // m: N x 1 + m, exact as N + m
+            acc[b][cc].mxy = __ffma2_rn(NN, mxy, acc[b][cc].mxy);
+            acc[b][cc].fxy = __ffma2_rn(make_float2(wz[cc], wz[cc]), A01,
+                                        __ffma2_rn(make_float2(dwz[cc], dwz[cc]), B01, acc[b][cc].fxy));
+            acc[b][cc].fz = fmaf(wz[cc], A2, fmaf(dwz[cc], B2, acc[b][cc].fz));
         }
     }
 }
@@ -208,13 +217,14 @@ __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, MPM_P2G_MINB) k_p2g_c
 #endif
 #pragma unroll 1
             for (int a = 0; a < 3; ++a) {
-                float acc[3][3][7];
+                NodeAcc acc[3][3];
 #pragma unroll
                 for (int b = 0; b < 3; ++b)
 #pragma unroll
-                    for (int cc = 0; cc < 3; ++cc)
-#pragma unroll
-                        for (int k = 0; k < 7; ++k) acc[b][cc][k] = 0.f;
+                    for (int cc = 0; cc < 3; ++cc) {
+                        acc[b][cc].m_mz = acc[b][cc].mxy = acc[b][cc].fxy = make_float2(0.f, 0.f);
+                        acc[b][cc].fz = 0.f;
+                    }
                 // round k: the k-th particle of every cell (both halves, in
                 // the block's k-major order)
                 int off = 0;
@@ -253,8 +263,14 @@ __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, MPM_P2G_MINB) k_p2g_c
                     for (int cc = 0; cc < 3; ++cc) {
                         if (cnt > 0) {
                             const int ti = (cx + a) + K::SY * (cy + b) + K::SZ * (cz + cc);
-#pragma unroll
-                            for (int k = 0; k < 7; ++k) tile[k][ti] += acc[b][cc][k];
+                            const NodeAcc& q = acc[b][cc];
+                            tile[0][ti] += q.m_mz.x;
+                            tile[1][ti] += q.mxy.x;
+                            tile[2][ti] += q.mxy.y;
+                            tile[3][ti] += q.m_mz.y;
+                            tile[4][ti] += q.fxy.x;
+                            tile[5][ti] += q.fxy.y;
+                            tile[6][ti] += q.fz;
                         }
                         __syncwarp();
                     }
