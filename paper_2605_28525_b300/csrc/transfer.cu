@@ -128,13 +128,14 @@ __device__ __forceinline__ void p2g_accumulate(const Params& P, const P2GIn& in,
     const float q0y = fmaf(hc[3], ox, in.v[1]) - hc[4] * d[1] - hc[5] * d[2];
     const float q0z = fmaf(hc[6], ox, in.v[2]) - hc[7] * d[1] - hc[8] * d[2];
     const float2 hc25 = make_float2(hc[2], hc[5]);
+    const float2 t01 = make_float2(t[0], t[1]), t13 = make_float2(t[1], t[3]), t24 = make_float2(t[2], t[4]);
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
         // tau . grad N over c: wz (tau_r0 dwx wy + tau_r1 wx dwy) + dwz tau_r2 wx wy
         const float Pw = wx * wy[b], Gx = dwx * wy[b], Gy = wx * dwy[b];
-        const float A0 = t[0] * Gx + t[1] * Gy, A1 = t[1] * Gx + t[3] * Gy, A2 = t[2] * Gx + t[4] * Gy;
-        const float B0 = t[2] * Pw, B1 = t[4] * Pw, B2 = t[5] * Pw;
-        const float2 A01 = make_float2(A0, A1), B01 = make_float2(B0, B1);
+        const float2 A01 = __ffma2_rn(t01, make_float2(Gx, Gx), __fmul2_rn(t13, make_float2(Gy, Gy)));
+        const float2 B01 = __fmul2_rn(t24, make_float2(Pw, Pw));
+        const float A2 = fmaf(t[2], Gx, t[4] * Gy), B2 = t[5] * Pw;
         const float2 qb = make_float2(fmaf(hc[1], (float)b, q0x), fmaf(hc[4], (float)b, q0y));
         const float qbz = fmaf(hc[7], (float)b, q0z);
 #pragma unroll
