@@ -101,6 +101,21 @@ struct P2GIn {
 
 // Adds one particle's contributions to the 9 nodes (a, 0..2, 0..2) of its
 // stencil: 7 channels (m, m v, f) per node, in units of m_p and -V0/h.
+// The y and z B-spline weights of one particle together, in packed FP32
+// (d = (d_y, d_z)); the same formulas as bspline3.
+__device__ __forceinline__ void bspline3_yz(float2 d, float wy[3], float dwy[3], float wz[3], float dwz[3]) {
+    const float2 t0 = __ffma2_rn(d, make_float2(-1.f, -1.f), make_float2(1.5f, 1.5f));   // 1.5 - d
+    const float2 t1 = __fadd2_rn(d, make_float2(-1.f, -1.f));
+    const float2 t2 = __fadd2_rn(d, make_float2(-0.5f, -0.5f));
+    const float2 w0 = __fmul2_rn(__fmul2_rn(make_float2(0.5f, 0.5f), t0), t0);
+    const float2 w1 = __ffma2_rn(__fmul2_rn(t1, make_float2(-1.f, -1.f)), t1, make_float2(0.75f, 0.75f));
+    const float2 w2 = __fmul2_rn(__fmul2_rn(make_float2(0.5f, 0.5f), t2), t2);
+    wy[0] = w0.x; wy[1] = w1.x; wy[2] = w2.x;
+    wz[0] = w0.y; wz[1] = w1.y; wz[2] = w2.y;
+    dwy[0] = -t0.x; dwy[1] = -2.f * t1.x; dwy[2] = t2.x;
+    dwz[0] = -t0.y; dwz[1] = -2.f * t1.y; dwz[2] = t2.y;
+}
+
 // The 7 channels of one node, paired for Blackwell's packed FP32 pipes
 // (__ffma2_rn: two FMAs per instruction, each rounded as fmaf):
 // (m, m v_z), (m v_x, m v_y), (f_x, f_y), f_z.
@@ -120,8 +135,7 @@ __device__ __forceinline__ void p2g_accumulate(const Params& P, const P2GIn& in,
     const float* t = in.t;
     float wx, dwx, wy[3], dwy[3], wz[3], dwz[3];
     bspline_a(d[0], a, wx, dwx);
-    bspline3(d[1], wy, dwy);
-    bspline3(d[2], wz, dwz);
+    bspline3_yz(make_float2(d[1], d[2]), wy, dwy, wz, dwz);
     // momentum at node (a, b, c): v + hC (a - dx, b - dy, c - dz)
     const float ox = (float)a - d[0];
     const float q0x = fmaf(hc[0], ox, in.v[0]) - hc[1] * d[1] - hc[2] * d[2];
