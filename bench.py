@@ -119,8 +119,8 @@ def alu_check(wl, phases: dict, sm_mhz):
     n = wl.n
     peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
     out = {"peak_tflops": peak, "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x median SM clock",
-           "flop_source": "per-particle FP32 operation count of the 1M Drucker-Prager column's ncu capture "
-                          "(profiles/flops.txt)"}
+           "flop_source": "per-particle FP32 operations (FFMA, FMUL, FADD and their packed forms) of the 1M "
+                          "Drucker-Prager column's ncu capture (profiles/flops.txt)"}
     for k in ("p2g", "g2p"):
         f = measured_flops_per_particle(k)
         if f is None:
