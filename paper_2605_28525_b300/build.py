@@ -20,6 +20,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmpm_b300.so")
+# the checked build: every indirect index of the hot kernels tested against its
+# buffer (MPM_CHECKED=1); same entry points, for validation runs
+CHECKED_LIB = os.path.join(HERE, "libmpm_b300_checked.so")
+CHECKED_OBJ = os.path.join(HERE, "_build_checked")
 HEADERS = [os.path.join(ROOT, "include", "mpm.h"), os.path.join(CSRC, "mpm_internal.cuh")]
 NVCC = "/usr/local/cuda/bin/nvcc"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -63,8 +67,16 @@ def build(force: bool = False, verbose: bool = False, out: str = LIB, obj_dir: s
     return out
 
 
+def build_checked(force: bool = False, verbose: bool = False) -> str:
+    """The checked library (MPM_CHECKED=1) beside the normal one."""
+    return build(force=force, verbose=verbose, out=CHECKED_LIB, obj_dir=CHECKED_OBJ, defines=("MPM_CHECKED=1",))
+
+
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
     ap.add_argument("--force", action="store_true")
+    ap.add_argument("--checked", action="store_true", help="also build the checked library")
     a = ap.parse_args()
     print(build(force=a.force, verbose=True))
+    if a.checked:
+        print(build_checked(force=a.force, verbose=True))

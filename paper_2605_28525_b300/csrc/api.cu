@@ -280,6 +280,7 @@ void update_live_cap(mpm_ctx* c) {
     live = std::min(live, c->node_cap / c->B3);
     if (c->det) live = std::min<int64_t>(live, c->tbuf_cap / (7 * 216));
     c->live_cap = live;
+    c->P.cap_blocks = (int)live;
 }
 
 // Clear the flags a step may raise and retry from (overflow, out of domain)
@@ -711,6 +712,7 @@ static mpm_status create_impl(const mpm_config* cfg, int64_t n, const float* x, 
     P.wall_layers = c->cfg.wall_layers;
     P.block_shift = c->B == 4 ? 2 : 0;
     P.max_probe = c->cfg.max_probe;
+    P.n_part = (int)n;
 
     CK(cudaMallocHost((void**)&c->hstat, sizeof(DevStatus)));
     std::memset(c->hstat, 0, sizeof(DevStatus));

@@ -73,6 +73,21 @@ __device__ __forceinline__ bool cta_aborted(const DevStatus* s) {
     return ab != 0u;
 }
 
+// The checked build (MPM_CHECKED=1, a separate library): an index outside the
+// buffer it addresses raises bit 4 of the map-error word (and the abort word)
+// and the access is skipped, so a bad index reports instead of corrupting
+// memory.  In the normal build the test compiles away.
+#ifndef MPM_CHECKED
+#define MPM_CHECKED 0
+#endif
+
+__device__ __forceinline__ bool index_ok(int64_t i, int64_t bound, DevStatus* st) {
+    if (!MPM_CHECKED) return true;
+    if (i >= 0 && i < bound) return true;
+    raise_flag(st, &st->map_miss, 4u);
+    return false;
+}
+
 // Live active-block count, clamped to the capacity the arrays were sized for.
 __device__ __forceinline__ int64_t live_blocks(const DevStatus* s, int64_t cap) {
     const int64_t n = (int64_t)s->n_active;
@@ -103,6 +118,9 @@ struct Params {
     int n_scen;                  // 1 for a single simulation
     int ens_pitch;               // blocks per scenario along x
     const uint32_t* scen_start;  // device, n_scen + 1 entries (nullptr when n_scen == 1)
+    // sizes the checked build tests indices against
+    int cap_blocks;              // blocks the per-block and grid arrays hold
+    int n_part;                  // particles
 };
 
 // Scenario of the particle with this id (binary search over scen_start).

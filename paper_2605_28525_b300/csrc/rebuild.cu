@@ -555,6 +555,7 @@ __device__ __forceinline__ uint32_t bin_key(int64_t p, int64_t n, const uint32_t
     if (p >= n) return 0xffffffffu;
     const uint32_t code = pcode[p];
     const uint32_t q = code / (uint32_t)B3;
+    if (code != 0xffffffffu && !hv.bits && !index_ok(q, (int64_t)hv.mask + 1, st)) return 0xffffffffu;
     const int r = code == 0xffffffffu ? -1 : (hv.bits ? mask_rank(hv, q) : hv.vals[q]);
     if (r < 0) {
         raise_flag(st, &st->map_miss, 1u);
@@ -794,7 +795,7 @@ constexpr int SCT_PL = MPM_SCATTER_PER_LANE;   // particles per lane in the scat
 __global__ void __launch_bounds__(256) k_bin_scatter(int64_t n, const uint32_t* __restrict__ key,
                                                      const uint32_t* __restrict__ prank, const int* __restrict__ cs,
                                                      uint32_t* __restrict__ skey, uint32_t* __restrict__ perm,
-                                                     const DevStatus* st) {
+                                                     DevStatus* st) {
     if (cta_aborted(st)) return;
     const int lane = threadIdx.x & 31;
     const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * SCT_PL + lane;
@@ -813,6 +814,7 @@ __global__ void __launch_bounds__(256) k_bin_scatter(int64_t n, const uint32_t* 
     for (int h = 0; h < SCT_PL; ++h) {
         if (k[h] == 0xffffffffu) continue;
         const int pos = cs[k[h]] + (int)r[h];
+        if (!index_ok(pos, n, st)) continue;
         skey[pos] = k[h];
         perm[pos] = (uint32_t)(p0 + 32 * h);
     }

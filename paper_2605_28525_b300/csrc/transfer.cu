@@ -204,6 +204,7 @@ __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, MPM_P2G_MINB) k_p2g_c
         u = __shfl_sync(FULL, u, 0);
         if (u >= nunits) break;
         const int r = pblocks[u / HU];
+        if (!index_ok(r, P.cap_blocks, st)) continue;
         const int h0 = DET ? 0 : u % HU, h1 = DET ? 2 : h0 + 1;
         const int zoff = (DET || by_count) ? 0 : 2 * h0;   // block z-layer of the tile's layer 0
         const int s = bstart[r], kcap = bend[r] - s;   // no cell holds more than the block's particles
@@ -263,6 +264,7 @@ __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, MPM_P2G_MINB) k_p2g_c
                             const int idx = h ? __popc(M0) + __popc(M1 & lt) : __popc(M0 & lt);
                             p = perm[s + off + idx];
                         }
+                        if (!index_ok(p, P.n_part, st)) continue;
                         P2GIn in;
                         in.load(ps, stride, p, P.h);
                         p2g_accumulate(P, in, a, acc);
@@ -321,6 +323,7 @@ __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, MPM_P2G_MINB) k_p2g_c
                 raise_flag(st, &st->map_miss, 1u);
                 continue;
             }
+            if (!index_ok(rank, P.cap_blocks, st)) continue;
             const int l = (tx & 3) + 4 * ((ty & 3) + 4 * (tz & 3));
             const int64_t g = (int64_t)rank * 64 + l;
             atomicAdd(&gmv[g], make_float4(v[0] * P.mp, v[1] * P.mp, v[2] * P.mp, v[3] * P.mp));
@@ -865,6 +868,7 @@ __device__ __forceinline__ void g2p_particle(const float* __restrict__ ps, float
                 const int lz = loc[2] + c;
                 const int ez = lz / B, mz = lz % B;
                 const int q = (B == 4) ? (ez ? q1 : q0) : (c == 0 ? q0 : (c == 1 ? q1 : q2));
+                if (!index_ok(q, P.cap_blocks, st)) continue;   // a stencil block must be in the table
                 const float4 v = __ldg(&gv[(int64_t)q * NC + mx + B * (my + B * mz)]);
                 Sw[0] = fmaf(wz[c], v.x, Sw[0]);
                 Sw[1] = fmaf(wz[c], v.y, Sw[1]);
@@ -961,7 +965,10 @@ __global__ void __launch_bounds__(THREADS, 65536 / (THREADS * REGS)) k_g2p(const
     if (cta_aborted(st)) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    g2p_particle<B, DENSE, MAT>(ps, po, stride, perm[i], i, (int)(skey[i] >> S3), nbr, P, gv, st);
+    const uint32_t p = perm[i];
+    const int r = (int)(skey[i] >> S3);
+    if (!index_ok(p, n, st) || !index_ok(r, P.cap_blocks, st)) return;
+    g2p_particle<B, DENSE, MAT>(ps, po, stride, p, i, r, nbr, P, gv, st);
 }
 
 

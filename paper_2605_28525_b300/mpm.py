@@ -19,7 +19,8 @@ import numpy as np
 from . import workloads as W
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libmpm_b300.so")
+# MPM_B300_LIB selects another build of the library (e.g. libmpm_b300_checked.so)
+LIB_PATH = os.environ.get("MPM_B300_LIB") or os.path.join(_HERE, "libmpm_b300.so")
 
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_HASH_OVERFLOW, ERR_OUT_OF_DOMAIN, ERR_NUMERIC, ERR_CUDA, ERR_STATE = range(8)
 NEOHOOKEAN, DRUCKER_PRAGER = 0, 1
