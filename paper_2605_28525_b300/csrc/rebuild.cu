@@ -19,9 +19,16 @@
 //                     Phi; the block's grid nodes are zeroed for P2G.
 //                     (k_assign: the same from a radix sort of the keys, for
 //                     boxes whose mask would be too large.)
-//   k_particle_keys   sort key (Phi(b(base)), l(base)) per particle.
-//   k_ranges          particle range of every block that holds particles and
-//                     the list of such blocks.
+//   k_neighbours      Phi of the blocks b + {0,1}^3 (b + {0,1,2}^3 for B = 1)
+//                     of every active block, for P2G and G2P.
+//   k_particle_keys   sort key (Phi(b(base)), l(base)) per particle, then a
+//                     radix sort (deterministic mode), and k_ranges: particle
+//                     range of every block that holds particles and the list
+//                     of such blocks.
+//   k_particle_bins   fast mode instead: a counting sort.  Bin (Phi, cell) and
+//   k_scan_tiles      rank in the bin per particle, a tile scan of the bins,
+//   k_bin_scatter     the scatter into (block, cell) order, then the particle
+//   k_block_ranges    ranges and the neighbour table in one pass.
 //   k_interleave      k-major particle order inside every block (the k-th
 //                     particle of each cell, then the next), and the particle
 //                     count per cell, for the cell-lane P2G.
@@ -252,6 +259,18 @@ __global__ void __launch_bounds__(256) k_dense_codes(const float* __restrict__ p
 }
 
 // Phi in key order: the sorted list position is the compact block index.
+// Tile scans (k_scan_tiles, k_bits_scan_tiles): each tile of SC_TILE items
+// is scanned locally, and the last CTA turns the tile totals into exclusive
+// tile offsets (tsum[ntiles] = the total).  Readers add the offset of the
+// item's tile themselves; there is no separate pass that adds it.
+constexpr int SC_THREADS = 256, SC_ITEMS = 8, SC_TILE = SC_THREADS * SC_ITEMS;
+
+// Exclusive prefix at item i (0 <= i <= n) of a tile scan over n items.
+__device__ __forceinline__ int scan_at(const int* __restrict__ local, const int* __restrict__ tsum, int64_t i,
+                                       int64_t n, int ntiles) {
+    return i < n ? local[i] + tsum[i / SC_TILE] : tsum[ntiles];
+}
+
 __global__ void k_assign(const uint32_t* __restrict__ skey, const uint32_t* __restrict__ sslot, int64_t cap,
                          const DevStatus* st, Params P, int* __restrict__ hvals, int4* __restrict__ bcoord,
                          float4* __restrict__ gmv, float4* __restrict__ gf, int* __restrict__ bins, int B3,
@@ -275,10 +294,13 @@ __global__ void k_assign(const uint32_t* __restrict__ skey, const uint32_t* __re
 }
 
 // Phi from the block bit mask: the rank of a key is the number of set bits
-// below it.  Thread i handles node i % B3 of the i / B3-th inserted block.
+// below it (the word's local prefix plus its tile's offset, then the bits
+// below it in the word).  Thread i handles node i % B3 of the i / B3-th
+// inserted block.
 __global__ void k_assign_bits(const uint32_t* __restrict__ akey, const uint32_t* __restrict__ aslot, int64_t cap,
                               const DevStatus* st, Params P, const uint32_t* __restrict__ bmask,
-                              const int* __restrict__ bpre, int* __restrict__ hvals, int4* __restrict__ bcoord,
+                              const int* __restrict__ bpre, const int* __restrict__ btsum,
+                              int* __restrict__ hvals, int4* __restrict__ bcoord,
                               float4* __restrict__ gmv, float4* __restrict__ gf, int* __restrict__ bins, int B3,
                               int zero_grid) {
     if (cta_aborted(st)) return;
@@ -289,7 +311,7 @@ __global__ void k_assign_bits(const uint32_t* __restrict__ akey, const uint32_t*
     const int l = (int)(i % B3);
     const uint32_t key = akey[q];
     const uint32_t w = key >> 5;
-    const int64_t r = (int64_t)bpre[w] + __popc(bmask[w] & ((1u << (key & 31u)) - 1u));
+    const int64_t r = (int64_t)bpre[w] + btsum[w / SC_TILE] + __popc(bmask[w] & ((1u << (key & 31u)) - 1u));
     if (l == 0) {
         hvals[aslot[q]] = (int)r;
         int bi, bj, bk;
@@ -442,7 +464,8 @@ __device__ __forceinline__ int first_geq(const uint32_t* __restrict__ skey, int 
 __global__ void __launch_bounds__(128) k_interleave(const uint32_t* __restrict__ skey, const uint32_t* __restrict__ perm,
                                                     const int* __restrict__ bstart, const int* __restrict__ bend,
                                                     const int* __restrict__ pblocks, const DevStatus* stc,
-                                                    const int* __restrict__ cs, uint32_t* __restrict__ skey2,
+                                                    const int* __restrict__ cs, const int* __restrict__ tsum,
+                                                    int ntiles, int64_t cap, uint32_t* __restrict__ skey2,
                                                     uint32_t* __restrict__ perm2, int* __restrict__ ccount,
                                                     uint8_t* __restrict__ cperm) {
     __shared__ unsigned char slot_cell[4][64];
@@ -458,10 +481,11 @@ __global__ void __launch_bounds__(128) k_interleave(const uint32_t* __restrict__
         const uint32_t base = (uint32_t)r * 64u;
         int lo0, hi0, lo1, hi1;
         if (cs) {   // cell starts known from the counting sort
-            lo0 = cs[base + lane];
-            hi0 = cs[base + lane + 1];
-            lo1 = cs[base + 32 + lane];
-            hi1 = cs[base + 33 + lane];
+            const int64_t n = live_blocks(stc, cap) * 64;
+            lo0 = scan_at(cs, tsum, base + lane, n, ntiles);
+            hi0 = scan_at(cs, tsum, base + lane + 1, n, ntiles);
+            lo1 = scan_at(cs, tsum, base + 32 + lane, n, ntiles);
+            hi1 = scan_at(cs, tsum, base + 33 + lane, n, ntiles);
         } else {
             lo0 = first_geq(skey, s, e, base + lane);
             hi0 = first_geq(skey, lo0, e, base + lane + 1);
@@ -642,7 +666,6 @@ __global__ void __launch_bounds__(256) k_particle_bins(int64_t n, const uint32_t
     }
 }
 
-constexpr int SC_THREADS = 256, SC_ITEMS = 8, SC_TILE = SC_THREADS * SC_ITEMS;
 
 // The end of a tile scan: every CTA has written its tile total to tsum; the
 // last CTA to arrive (counted on `counter`, which it resets) turns the
@@ -687,9 +710,9 @@ __device__ __forceinline__ void finish_tile_sums(int* __restrict__ tsum, int nti
 }
 
 // Exclusive scan of the live bins (live blocks x B3; the grid covers the
-// capacity), steps 1 and 2: each tile of 2048 bins scanned locally, tile
-// totals (zero for tiles past the live bins) turned into tile offsets by the
-// last CTA.
+// capacity): each tile of 2048 bins scanned locally, tile totals (zero for
+// tiles past the live bins) turned into tile offsets by the last CTA.  A
+// bin's start is scan_at(cs, tsum, ...).
 __global__ void __launch_bounds__(SC_THREADS) k_scan_tiles(const int* __restrict__ in, int64_t cap, int B3,
                                                            DevStatus* st, int* __restrict__ out,
                                                            int* __restrict__ tsum) {
@@ -730,18 +753,8 @@ __global__ void __launch_bounds__(SC_THREADS) k_scan_tiles(const int* __restrict
     finish_tile_sums(tsum, (int)gridDim.x, &st->scan_done[1]);
 }
 
-// Step 3: add the tile offsets; cs[n] = total.
-__global__ void k_scan_add(int* __restrict__ cs, int64_t cap, int B3, const DevStatus* st,
-                           const int* __restrict__ tsum, int ntiles) {
-    if (cta_aborted(st)) return;
-    const int64_t n = live_blocks(st, cap) * B3;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) cs[i] += tsum[i / SC_TILE];
-    if (i == n) cs[n] = tsum[ntiles];
-}
-
 // Exclusive scan of the bit counts of the block mask's words, steps 1 and 2
-// (step 3 is k_scan_add_n).
+// (step 3, k_scan_add_n, only where lookups read the scan: scan mode).
 __global__ void __launch_bounds__(SC_THREADS) k_bits_scan_tiles(const uint32_t* __restrict__ bmask, int64_t n,
                                                                 DevStatus* st, int* __restrict__ out,
                                                                 int* __restrict__ tsum) {
@@ -794,8 +807,8 @@ constexpr int SCT_PL = MPM_SCATTER_PER_LANE;   // particles per lane in the scat
 // ... within the warp's 32 x SCT_PL) for as many load chains in flight.
 __global__ void __launch_bounds__(256) k_bin_scatter(int64_t n, const uint32_t* __restrict__ key,
                                                      const uint32_t* __restrict__ prank, const int* __restrict__ cs,
-                                                     uint32_t* __restrict__ skey, uint32_t* __restrict__ perm,
-                                                     DevStatus* st) {
+                                                     const int* __restrict__ tsum, uint32_t* __restrict__ skey,
+                                                     uint32_t* __restrict__ perm, DevStatus* st) {
     if (cta_aborted(st)) return;
     const int lane = threadIdx.x & 31;
     const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * SCT_PL + lane;
@@ -813,27 +826,39 @@ __global__ void __launch_bounds__(256) k_bin_scatter(int64_t n, const uint32_t* 
 #pragma unroll
     for (int h = 0; h < SCT_PL; ++h) {
         if (k[h] == 0xffffffffu) continue;
-        const int pos = cs[k[h]] + (int)r[h];
+        const int pos = cs[k[h]] + tsum[k[h] / SC_TILE] + (int)r[h];   // a particle's bin is live
         if (!index_ok(pos, n, st)) continue;
         skey[pos] = k[h];
         perm[pos] = (uint32_t)(p0 + 32 * h);
     }
 }
 
-// Particle range and flag of every active block from the cell starts.
-__global__ void k_block_ranges(int64_t cap, int B3, const int* __restrict__ cs, int* __restrict__ bstart,
-                               int* __restrict__ bend, int* __restrict__ pblocks, int* __restrict__ hasp,
-                               DevStatus* st) {
+// Counting-sort mode: the neighbour table of every active block (as
+// k_neighbours: thread t looks up neighbour t % NNB of block t / NNB), and,
+// in the thread of neighbour 0, the block's particle range and flag from its
+// cell starts.
+template <int B>
+__global__ void k_block_ranges(int64_t cap, int B3, const int* __restrict__ cs, const int* __restrict__ tsum,
+                               int ntiles, int* __restrict__ bstart, int* __restrict__ bend,
+                               int* __restrict__ pblocks, int* __restrict__ hasp, DevStatus* st,
+                               const int4* __restrict__ bcoord, Params P, HashView hv, int* __restrict__ nbr) {
+    constexpr int R = (B == 4) ? 2 : 3;
+    constexpr int NNB = R * R * R;
     if (cta_aborted(st)) return;
     const int64_t nact = live_blocks(st, cap);
-    const int gen = (int)st->gen;
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nact) return;
-    const int s = cs[r * B3], e = cs[r * B3 + B3];
-    if (e > s) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nact * NNB) return;
+    const int64_t r = t / NNB;
+    const int e = (int)(t % NNB);
+    const int4 b = bcoord[r];
+    nbr[t] = lookup_block(P, hv, b.x + e / (R * R), b.y + (e / R) % R, b.z + e % R);
+    if (e != 0) return;
+    const int64_t n = nact * B3;
+    const int s = scan_at(cs, tsum, r * B3, n, ntiles), en = scan_at(cs, tsum, r * B3 + B3, n, ntiles);
+    if (en > s) {
         bstart[r] = s;
-        bend[r] = e;
-        hasp[r] = gen;
+        bend[r] = en;
+        hasp[r] = (int)st->gen;
         pblocks[atomicAdd(&st->n_pblocks, 1u)] = (int)r;
     }
 }
@@ -912,11 +937,10 @@ cudaError_t launch_assign(mpm_ctx* c) {
     } else if (c->bmask) {
         const int ntiles = (int)((c->bwords + SC_TILE - 1) / SC_TILE);
         k_bits_scan_tiles<<<ntiles, SC_THREADS, 0, c->ls>>>(c->bmask, c->bwords, c->dstat, c->bpre, c->btsum);
-        k_scan_add_n<<<blocks_for(c->bwords + 1, 256), 256, 0, c->ls>>>(c->bpre, c->bwords, c->dstat, c->btsum, ntiles);
         k_assign_bits<<<blocks_for(cap * c->B3, 256), 256, 0, c->ls>>>(c->akey[0], c->aslot[0], cap, c->dstat, c->P,
-                                                                       c->bmask, c->bpre, c->hvals, c->bcoord, c->gmv,
-                                                                       c->gf, bins, c->B3, zero);
-        c->launches += 3;
+                                                                       c->bmask, c->bpre, c->btsum, c->hvals,
+                                                                       c->bcoord, c->gmv, c->gf, bins, c->B3, zero);
+        c->launches += 2;
     } else {
         const int bits = 64 - __builtin_clzll((unsigned long long)(c->n_dom_blocks > 1 ? c->n_dom_blocks - 1 : 1));
         int sel = radix_sort_pairs(c, c->akey, c->aslot, cap, &c->dstat->n_active, bits, c->ls, &c->dstat->abort);
@@ -925,6 +949,7 @@ cudaError_t launch_assign(mpm_ctx* c) {
                                                                   zero);
         ++c->launches;
     }
+    if (counting_sort(c)) return cudaGetLastError();   // the neighbour table comes with the block ranges
     const HashView hv = hash_view(c);
     const int nnb = c->B == 4 ? 8 : 27;
     if (c->B == 4)
@@ -947,10 +972,9 @@ cudaError_t launch_particle_keys(mpm_ctx* c) {
                                                                   c->prank, c->dstat);
         const int ntiles = (int)((nkeys + SC_TILE - 1) / SC_TILE);
         k_scan_tiles<<<ntiles, SC_THREADS, 0, c->ls>>>(c->bins, cap, c->B3, c->dstat, c->cs, c->tsum);
-        k_scan_add<<<blocks_for(nkeys + 1, 256), 256, 0, c->ls>>>(c->cs, cap, c->B3, c->dstat, c->tsum, ntiles);
-        k_bin_scatter<<<blocks_for(c->n, 256 * SCT_PL), 256, 0, c->ls>>>(c->n, c->pkey[0], c->prank, c->cs, c->pkey[1],
-                                                                c->pval[1], c->dstat);
-        c->launches += 4;
+        k_bin_scatter<<<blocks_for(c->n, 256 * SCT_PL), 256, 0, c->ls>>>(c->n, c->pkey[0], c->prank, c->cs, c->tsum,
+                                                                         c->pkey[1], c->pval[1], c->dstat);
+        c->launches += 3;
         c->sorted_sel = 1;
         return cudaGetLastError();
     }
@@ -972,9 +996,17 @@ cudaError_t launch_particle_keys(mpm_ctx* c) {
 cudaError_t launch_ranges(mpm_ctx* c, const uint32_t* skey) {
     const bool cnt = counting_sort(c);
     const int64_t cap = c->live_cap;
+    const int ntiles = (int)((cap * c->B3 + SC_TILE - 1) / SC_TILE);   // the bin scan's tiles
     if (cnt) {
-        k_block_ranges<<<blocks_for(cap, 256), 256, 0, c->ls>>>(cap, c->B3, c->cs, c->bstart, c->bend, c->pblocks,
-                                                                c->hasp, c->dstat);
+        const HashView hv = hash_view(c);
+        if (c->B == 4)
+            k_block_ranges<4><<<blocks_for(cap * 8, 256), 256, 0, c->ls>>>(
+                cap, c->B3, c->cs, c->tsum, ntiles, c->bstart, c->bend, c->pblocks, c->hasp, c->dstat, c->bcoord, c->P,
+                hv, c->nbr);
+        else
+            k_block_ranges<1><<<blocks_for(cap * 27, 256), 256, 0, c->ls>>>(
+                cap, c->B3, c->cs, c->tsum, ntiles, c->bstart, c->bend, c->pblocks, c->hasp, c->dstat, c->bcoord, c->P,
+                hv, c->nbr);
     } else {
         const int shift = (c->B == 4) ? 6 : 0;
         k_ranges<<<blocks_for(c->n, 256), 256, 0, c->ls>>>(skey, c->n, shift, cap, c->bstart, c->bend, c->pblocks,
@@ -984,8 +1016,8 @@ cudaError_t launch_ranges(mpm_ctx* c, const uint32_t* skey) {
     if (c->B == 4) {
         const int o = 1 - c->sorted_sel;
         k_interleave<<<148 * 8, 128, 0, c->ls>>>(skey, c->pval[c->sorted_sel], c->bstart, c->bend, c->pblocks, c->dstat,
-                                                cnt ? c->cs : nullptr, c->pkey[o], c->pval[o], c->ccount,
-                                                cnt ? c->cperm : nullptr);
+                                                cnt ? c->cs : nullptr, c->tsum, ntiles, cap, c->pkey[o], c->pval[o],
+                                                c->ccount, cnt ? c->cperm : nullptr);
         c->sorted_sel = o;
         ++c->launches;
     }
