@@ -197,6 +197,9 @@ __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, MPM_P2G_MINB) k_p2g_c
 
     for (int i = lane; i < 7 * K::TILE; i += 32) (&tile[0][0])[i] = 0.f;
     __syncwarp();
+    // Map errors are noted here and raised once at the end: a flag raise
+    // (two atomics) inside the loops would constrain how they are scheduled.
+    unsigned int miss = 0u;
 
     for (;;) {
         int u = 0;
@@ -248,7 +251,7 @@ __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, MPM_P2G_MINB) k_p2g_c
                     const unsigned M0 = __ballot_sync(FULL, cnt0 > k), M1 = __ballot_sync(FULL, cnt1 > k);
                     if ((M0 | M1) == 0u) break;
                     if (k >= kcap || off + __popc(M0) + __popc(M1) > kcap) {   // inconsistent counts
-                        if (lane == 0) raise_flag(st, &st->map_miss, 2u);
+                        miss |= 2u;
                         break;
                     }
                     if (cnt > k) {
@@ -320,7 +323,7 @@ __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, MPM_P2G_MINB) k_p2g_c
             if (DENSE) rank = r + (ex * P.nb[1] + ey) * P.nb[2] + ez;
             else rank = __ldg(&nbr[(int64_t)r * 8 + (ex * 2 + ey) * 2 + ez]);
             if (rank < 0) {
-                raise_flag(st, &st->map_miss, 1u);
+                miss |= 1u;
                 continue;
             }
             if (!index_ok(rank, P.cap_blocks, st)) continue;
@@ -331,6 +334,7 @@ __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, MPM_P2G_MINB) k_p2g_c
         }
         __syncwarp();
     }
+    if (miss) raise_flag(st, &st->map_miss, miss);
 }
 
 // --------------------------------------------- P2G: deterministic reduce
@@ -942,7 +946,7 @@ __device__ __forceinline__ void g2p_particle(const float* __restrict__ ps, float
         sum += Fn[k];
         po[(PF + k) * stride + i] = Fn[k];
     }
-    if (!(ok && isfinite(sum))) raise_flag(st, &st->numeric, 1u);
+    const bool bad = !(ok && isfinite(sum));
     po[(PT + 0) * stride + i] = tau.xx;
     po[(PT + 1) * stride + i] = tau.xy;
     po[(PT + 2) * stride + i] = tau.xz;
@@ -951,6 +955,7 @@ __device__ __forceinline__ void g2p_particle(const float* __restrict__ ps, float
     po[(PT + 5) * stride + i] = tau.zz;
     po[PPHI * stride + i] = alpha;
     po[PID * stride + i] = ps[PID * stride + p];
+    if (bad) raise_flag(st, &st->numeric, 1u);   // after the stores, which it then does not hold back
 }
 
 // THREADS x REGS: the CTA size and the registers a thread is compiled for
