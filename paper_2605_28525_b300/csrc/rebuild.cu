@@ -74,11 +74,25 @@ __global__ void k_status_clear(DevStatus* st, unsigned int n_dom_blocks) {
     st->gen += 1u;
 }
 
+// Flags found while a thread works through its particles are collected as
+// bits and raised once at the end of the kernel (raise_errors): a flag raise
+// (two atomics) inside the per-particle code would constrain how its loads
+// and probes are scheduled.
+enum : unsigned { ERR_NUMERIC = 1u, ERR_DOMAIN = 2u, ERR_PROBE = 4u, ERR_LIST = 8u };
+
+__device__ __forceinline__ void raise_errors(DevStatus* st, unsigned err) {
+    if (!err) return;
+    if (err & ERR_NUMERIC) raise_flag(st, &st->numeric, 1u);
+    if (err & ERR_DOMAIN) raise_flag(st, &st->out_of_domain, 1u);
+    if (err & ERR_PROBE) raise_flag(st, &st->overflow, 1u);
+    if (err & ERR_LIST) raise_flag(st, &st->overflow, 2u);
+}
+
 // Alg. 6 for one key; returns the slot holding it or -1 when n_probe slots
 // were all taken by other keys (overflow).
 __device__ int hash_insert(const HashView& hv, uint64_t key, uint32_t rkey, int max_probe,
                            uint32_t* __restrict__ akey, uint32_t* __restrict__ aslot, int64_t cap,
-                           uint32_t* __restrict__ bmask, DevStatus* st) {
+                           uint32_t* __restrict__ bmask, DevStatus* st, unsigned& err) {
     uint64_t s = mix64(key) & hv.mask;
     for (int r = 0; r < max_probe; ++r) {
         unsigned long long cur = *((volatile unsigned long long*)&hv.keys[s]);
@@ -97,7 +111,7 @@ __device__ int hash_insert(const HashView& hv, uint64_t key, uint32_t rkey, int 
                     akey[idx] = rkey;
                     aslot[idx] = (uint32_t)s;
                 } else {
-                    raise_flag(st, &st->overflow, 2u);
+                    err |= ERR_LIST;
                 }
                 return (int)s;
             }
@@ -105,26 +119,26 @@ __device__ int hash_insert(const HashView& hv, uint64_t key, uint32_t rkey, int 
         }
         s = (s + 1) & hv.mask;
     }
-    raise_flag(st, &st->overflow, 1u);
+    err |= ERR_PROBE;
     return -1;
 }
 
-// Reads x, checks it and computes the stencil base node; false if the
-// particle is unusable (flags set).
-__device__ __forceinline__ bool particle_base_x(const float x[3], const Params& P, int base[3], DevStatus* st) {
+// Checks x and computes the stencil base node; false if the particle is
+// unusable (error bits set).
+__device__ __forceinline__ bool particle_base_x(const float x[3], const Params& P, int base[3], unsigned& err) {
     bool ok = true;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         float fx = x[a] * P.inv_h;
         if (!isfinite(fx)) {
-            raise_flag(st, &st->numeric, 1u);
+            err |= ERR_NUMERIC;
             ok = false;
             base[a] = 0;
             continue;
         }
         // the stencil base..base+2 must lie inside the node box
         if (!(fx >= (float)P.lo[a] + 0.5f && fx < (float)(P.hi[a] - 2) + 1.5f)) {
-            raise_flag(st, &st->out_of_domain, 1u);
+            err |= ERR_DOMAIN;
             ok = false;
             base[a] = 0;
             continue;
@@ -135,9 +149,9 @@ __device__ __forceinline__ bool particle_base_x(const float x[3], const Params& 
 }
 
 __device__ __forceinline__ bool particle_base(const float* __restrict__ ps, int64_t stride, int64_t p,
-                                              const Params& P, int base[3], DevStatus* st) {
+                                              const Params& P, int base[3], unsigned& err) {
     const float x[3] = {ps[(PX + 0) * stride + p], ps[(PX + 1) * stride + p], ps[(PX + 2) * stride + p]};
-    return particle_base_x(x, P, base, st);
+    return particle_base_x(x, P, base, err);
 }
 
 // SCAN: the scan realisation (Sec. 4.2, Alg. 2): each needed block's bit is
@@ -150,7 +164,7 @@ __device__ __forceinline__ void insert_particle(const float* __restrict__ ps, in
                                                 const float x[3], const Params& P, const HashView& hv,
                                                 uint32_t* __restrict__ akey, uint32_t* __restrict__ aslot,
                                                 int64_t cap, uint32_t* __restrict__ bmask,
-                                                uint32_t* __restrict__ pcode, DevStatus* st) {
+                                                uint32_t* __restrict__ pcode, DevStatus* st, unsigned& err) {
     constexpr int S = (B == 4) ? 2 : 0;
     constexpr int R = (B == 4) ? 2 : 3;   // blocks a stencil can span per axis
     constexpr int NJ = R * R * R;
@@ -158,7 +172,7 @@ __device__ __forceinline__ void insert_particle(const float* __restrict__ ps, in
     const unsigned FULL = 0xffffffffu;
     int base[3] = {0, 0, 0};
     bool ok = p < n;
-    if (ok) ok = particle_base_x(x, P, base, st);
+    if (ok) ok = particle_base_x(x, P, base, err);
     int b0[3];
     unsigned need = 0;   // bit j: block b0 + (j / R^2, (j / R) % R, j % R) holds a stencil node
 #pragma unroll
@@ -204,7 +218,7 @@ __device__ __forceinline__ void insert_particle(const float* __restrict__ ps, in
                 slot = (int)rk;
             } else {
                 slot = hash_insert(hv, pack_key(bi, bj, bk), rel_key(P, bi, bj, bk), P.max_probe, akey, aslot, cap,
-                                   bmask, st);
+                                   bmask, st, err);
             }
             if (j == 0) myslot = slot;   // offset 0 (the base block) is taken by rank 0 = the leader
         }
@@ -238,9 +252,11 @@ __global__ void __launch_bounds__(256) k_insert(const float* __restrict__ ps, in
     for (int h = 0; h < INS_PL; ++h)
 #pragma unroll
         for (int a = 0; a < 3; ++a) xs[h][a] = (p0 + 32 * h < n) ? ps[(PX + a) * stride + p0 + 32 * h] : 0.f;
+    unsigned err = 0u;
 #pragma unroll
     for (int h = 0; h < INS_PL; ++h)
-        insert_particle<B, SCAN>(ps, stride, n, p0 + 32 * h, xs[h], P, hv, akey, aslot, cap, bmask, pcode, st);
+        insert_particle<B, SCAN>(ps, stride, n, p0 + 32 * h, xs[h], P, hv, akey, aslot, cap, bmask, pcode, st, err);
+    raise_errors(st, err);
 }
 
 // Dense comparator: the identity map.  The particle's sort key is the block's
@@ -253,7 +269,11 @@ __global__ void __launch_bounds__(256) k_dense_codes(const float* __restrict__ p
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     int base[3];
-    if (!particle_base(ps, stride, p, P, base, st)) return;
+    unsigned err = 0u;
+    if (!particle_base(ps, stride, p, P, base, err)) {
+        raise_errors(st, err);
+        return;
+    }
     const int cell = (base[0] & (B - 1)) + B * ((base[1] & (B - 1)) + B * (base[2] & (B - 1)));
     pcode[p] = rel_key(P, base[0] >> S, base[1] >> S, base[2] >> S) * (uint32_t)(B * B * B) + (uint32_t)cell;
 }
@@ -575,14 +595,14 @@ __global__ void __launch_bounds__(128) k_interleave(const uint32_t* __restrict__
 // atomic add by their leader.  Each warp takes 64 consecutive particles, two
 // per lane, so that two chains of dependent loads are in flight per lane.
 __device__ __forceinline__ uint32_t bin_key(int64_t p, int64_t n, const uint32_t* __restrict__ pcode,
-                                            const HashView& hv, int B3, DevStatus* st) {
+                                            const HashView& hv, int B3, DevStatus* st, bool& miss) {
     if (p >= n) return 0xffffffffu;
     const uint32_t code = pcode[p];
     const uint32_t q = code / (uint32_t)B3;
     if (code != 0xffffffffu && !hv.bits && !index_ok(q, (int64_t)hv.mask + 1, st)) return 0xffffffffu;
     const int r = code == 0xffffffffu ? -1 : (hv.bits ? mask_rank(hv, q) : hv.vals[q]);
     if (r < 0) {
-        raise_flag(st, &st->map_miss, 1u);
+        miss = true;   // raised by the caller once both keys are known
         return 0xffffffffu;
     }
     return (uint32_t)r * (uint32_t)B3 + code % (uint32_t)B3;
@@ -619,7 +639,9 @@ __global__ void __launch_bounds__(256) k_particle_bins(int64_t n, const uint32_t
     if (cta_aborted(st)) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * 2 + lane, p1 = p0 + 32;
-    const uint32_t k0 = bin_key(p0, n, pcode, hv, B3, st), k1 = bin_key(p1, n, pcode, hv, B3, st);
+    bool miss = false;
+    const uint32_t k0 = bin_key(p0, n, pcode, hv, B3, st, miss), k1 = bin_key(p1, n, pcode, hv, B3, st, miss);
+    if (miss) raise_flag(st, &st->map_miss, 1u);
     // key range of the CTA's valid keys (invalid keys are all ones)
     const uint32_t lo = min(k0, k1);
     const uint32_t hi = max(k0 == 0xffffffffu ? 0u : k0, k1 == 0xffffffffu ? 0u : k1);
