@@ -189,6 +189,9 @@ __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, MPM_P2G_MINB) k_p2g_c
     const bool by_count = !DET && cperm != nullptr;
     const int TZ = (DET || by_count) ? K::T : 4;
     __shared__ float tiles[K::WARPS][7][K::TILE];
+#if MPM_P2G_PCACHE
+    __shared__ uint32_t pcs[K::WARPS][MPM_P2G_PCACHE][32];   // the lanes' cached particle indices
+#endif
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     float(&tile)[7][K::TILE] = tiles[wid];
     if (cta_aborted(stc)) return;
@@ -220,8 +223,8 @@ __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, MPM_P2G_MINB) k_p2g_c
             const int cx = cell & 3, cy = (cell >> 2) & 3, cz = (cell >> 4) - zoff;
 #if MPM_P2G_PCACHE
             // storage indices of this lane's first rounds, loaded once for the
-            // three x-offset passes (one dependent load less per round)
-            uint32_t pc[MPM_P2G_PCACHE];
+            // three x-offset passes (one dependent load less per round) and
+            // kept in shared memory: a round reads its index with one load
             {
                 int off = 0;
 #pragma unroll
@@ -229,9 +232,10 @@ __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, MPM_P2G_MINB) k_p2g_c
                     const unsigned M0 = __ballot_sync(FULL, cnt0 > k), M1 = __ballot_sync(FULL, cnt1 > k);
                     const int idx = h ? __popc(M0) + __popc(M1 & lt) : __popc(M0 & lt);
                     const int nrun = __popc(M0) + __popc(M1);
-                    pc[k] = (cnt > k && off + nrun <= kcap) ? perm[s + off + idx] : 0u;
+                    pcs[wid][k][lane] = (cnt > k && off + nrun <= kcap) ? perm[s + off + idx] : 0u;
                     off += nrun;
                 }
+                __syncwarp();
             }
 #endif
 #pragma unroll 1
@@ -257,11 +261,9 @@ __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, MPM_P2G_MINB) k_p2g_c
                     if (cnt > k) {
                         uint32_t p;
 #if MPM_P2G_PCACHE
-                        if (k < MPM_P2G_PCACHE) {
-                            p = pc[0];
-#pragma unroll
-                            for (int q = 1; q < MPM_P2G_PCACHE; ++q) p = (k == q) ? pc[q] : p;
-                        } else
+                        if (k < MPM_P2G_PCACHE)
+                            p = pcs[wid][k][lane];
+                        else
 #endif
                         {
                             const int idx = h ? __popc(M0) + __popc(M1 & lt) : __popc(M0 & lt);
