@@ -168,7 +168,7 @@ __device__ __forceinline__ void p2g_accumulate(const Params& P, const P2GIn& in,
 }
 
 #ifndef MPM_P2G_PCACHE
-#define MPM_P2G_PCACHE 8   // rounds whose particle indices a lane loads once per work unit
+#define MPM_P2G_PCACHE 12   // rounds whose particle indices a lane loads once per work unit
 #endif
 
 template <bool DENSE, bool DET>
