@@ -315,16 +315,23 @@ def time_steps(sim, nsteps, flush=None):
 
 def time_phases(sim, nsteps, flush=None):
     """Device time (ms) of each phase of the step, through the phase entry
-    points (same kernels as sim.step)."""
+    points (same kernels as sim.step).  The rebuild reads its status on the
+    host, so the GPU would go idle until the host has queued P2G; a fixed
+    clock wait on the GPU (torch.cuda._sleep, about 0.1 ms, outside every
+    interval) lets the host queue P2G, the grid update and G2P first, so that
+    no host latency falls inside their intervals.  The rebuild interval
+    includes its own status read."""
     import torch
     st = torch.cuda.current_stream()
     acc = {"rebuild": [], "p2g": [], "grid": [], "g2p": []}
     for _ in range(nsteps):
         if flush is not None:
             flush.zero_()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
         ev[0].record(st)
         sim.rebuild_active()
+        ev[5].record(st)
+        torch.cuda._sleep(200000)
         ev[1].record(st)
         sim.p2g()
         ev[2].record(st)
@@ -333,7 +340,8 @@ def time_phases(sim, nsteps, flush=None):
         sim.g2p()
         ev[4].record(st)
         ev[4].synchronize()
-        for k, name in enumerate(("rebuild", "p2g", "grid", "g2p")):
+        acc["rebuild"].append(ev[0].elapsed_time(ev[5]))
+        for k, name in ((1, "p2g"), (2, "grid"), (3, "g2p")):
             acc[name].append(ev[k].elapsed_time(ev[k + 1]))
     return {k: float(np.mean(v)) for k, v in acc.items()}
 
