@@ -154,80 +154,107 @@ __device__ __forceinline__ bool particle_base(const float* __restrict__ ps, int6
     return particle_base_x(x, P, base, err);
 }
 
-// SCAN: the scan realisation (Sec. 4.2, Alg. 2): each needed block's bit is
-// set in the mask and the particle's code holds its base block's relative key;
-// no table.  Otherwise Alg. 6 as above, and the code holds the table slot.
-// One particle p (coordinates x already loaded when p < n); every lane of the
-// warp calls it.
-template <int B, bool SCAN>
-__device__ __forceinline__ void insert_particle(const float* __restrict__ ps, int64_t stride, int64_t n, int64_t p,
-                                                const float x[3], const Params& P, const HashView& hv,
-                                                uint32_t* __restrict__ akey, uint32_t* __restrict__ aslot,
-                                                int64_t cap, uint32_t* __restrict__ bmask,
-                                                uint32_t* __restrict__ pcode, DevStatus* st, unsigned& err) {
+// The stencil of one particle: its base block b0 (shifted by its scenario's
+// pitch in an ensemble), the mask of the blocks b0 + {0..R-1}^3 that hold
+// one of its 27 nodes, the key of b0 (EMPTY_KEY for an unusable particle or
+// p >= n) and its cell in b0.
+template <int B>
+struct Stencil {
+    int b0[3];
+    unsigned need;   // bit j: block b0 + (j / R^2, (j / R) % R, j % R) holds a stencil node
+    uint64_t key0;
+    int cell;
+    bool ok;
+};
+
+template <int B>
+__device__ __forceinline__ Stencil<B> particle_stencil(const float* __restrict__ ps, int64_t stride, int64_t n,
+                                                       int64_t p, const float x[3], const Params& P, unsigned& err) {
     constexpr int S = (B == 4) ? 2 : 0;
     constexpr int R = (B == 4) ? 2 : 3;   // blocks a stencil can span per axis
     constexpr int NJ = R * R * R;
-    const int lane = threadIdx.x & 31;
-    const unsigned FULL = 0xffffffffu;
+    Stencil<B> t;
     int base[3] = {0, 0, 0};
-    bool ok = p < n;
-    if (ok) ok = particle_base_x(x, P, base, err);
-    int b0[3];
-    unsigned need = 0;   // bit j: block b0 + (j / R^2, (j / R) % R, j % R) holds a stencil node
+    t.ok = p < n;
+    if (t.ok) t.ok = particle_base_x(x, P, base, err);
+    t.need = 0;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) b0[a] = base[a] >> S;
-    if (ok) {
+    for (int a = 0; a < 3; ++a) t.b0[a] = base[a] >> S;
+    if (t.ok) {
         int nbk[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) nbk[a] = ((base[a] + 2) >> S) - b0[a] + 1;
+        for (int a = 0; a < 3; ++a) nbk[a] = ((base[a] + 2) >> S) - t.b0[a] + 1;
 #pragma unroll
         for (int j = 0; j < NJ; ++j)
-            if (j / (R * R) < nbk[0] && (j / R) % R < nbk[1] && j % R < nbk[2]) need |= 1u << j;
+            if (j / (R * R) < nbk[0] && (j / R) % R < nbk[1] && j % R < nbk[2]) t.need |= 1u << j;
     }
     // An ensemble's scenario s has its blocks ens_pitch * s further along x.
-    if (P.n_scen > 1 && ok) b0[0] += scenario_of(P, __float_as_uint(ps[PID * stride + p])) * P.ens_pitch;
-    // Lanes with the same base block form one group (particles are sorted, so
-    // a warp usually holds one group).  The group's union of needed blocks is
-    // one OR reduction (one ballot per block offset when the warp holds several
-    // groups), and member r inserts offsets r, r + group size, ..., so the CAS
-    // probes of one warp run in parallel.
-    const uint64_t key0 = ok ? pack_key(b0[0], b0[1], b0[2]) : EMPTY_KEY;
-    const unsigned peers = __match_any_sync(FULL, key0);
+    if (P.n_scen > 1 && t.ok) t.b0[0] += scenario_of(P, __float_as_uint(ps[PID * stride + p])) * P.ens_pitch;
+    t.key0 = t.ok ? pack_key(t.b0[0], t.b0[1], t.b0[2]) : EMPTY_KEY;
+    t.cell = (base[0] & (B - 1)) + B * ((base[1] & (B - 1)) + B * (base[2] & (B - 1)));
+    return t;
+}
+
+// SCAN: the scan realisation (Sec. 4.2, Alg. 2): the block's bit is set in
+// the mask and its "slot" is its relative key; no table.  Otherwise Alg. 6
+// (hash_insert) and the table slot.  Block b0 + offset j.
+template <int B, bool SCAN>
+__device__ __forceinline__ int insert_block(const Params& P, const HashView& hv, const int b0[3], int j,
+                                            uint32_t* __restrict__ akey, uint32_t* __restrict__ aslot, int64_t cap,
+                                            uint32_t* __restrict__ bmask, DevStatus* st, unsigned& err) {
+    constexpr int R = (B == 4) ? 2 : 3;
+    const int bi = b0[0] + j / (R * R), bj = b0[1] + (j / R) % R, bk = b0[2] + j % R;
+    if (SCAN) {
+        const uint32_t rk = rel_key(P, bi, bj, bk), bit = 1u << (rk & 31u);
+        if (!(*((volatile uint32_t*)&bmask[rk >> 5]) & bit)) atomicOr(&bmask[rk >> 5], bit);
+        return (int)rk;
+    }
+    return hash_insert(hv, pack_key(bi, bj, bk), rel_key(P, bi, bj, bk), P.max_probe, akey, aslot, cap, bmask, st,
+                       err);
+}
+
+__device__ __forceinline__ void write_code(uint32_t* __restrict__ pcode, int64_t p, bool ok, int slot0, int cell,
+                                           int B3) {
+    if (ok) pcode[p] = slot0 < 0 ? 0xffffffffu : (uint32_t)slot0 * (uint32_t)B3 + (uint32_t)cell;
+}
+
+// One particle per lane (every lane of the warp calls it).  Lanes with the
+// same base block form one group (particles are sorted, so a warp usually
+// holds one group).  The group's union of needed blocks is one OR reduction
+// (one ballot per block offset when the warp holds several groups), and
+// member r inserts offsets r, r + group size, ..., so the probes of one warp
+// run in parallel.
+template <int B, bool SCAN>
+__device__ __forceinline__ void insert_group(const Stencil<B>& t, int64_t p, const Params& P, const HashView& hv,
+                                             uint32_t* __restrict__ akey, uint32_t* __restrict__ aslot, int64_t cap,
+                                             uint32_t* __restrict__ bmask, uint32_t* __restrict__ pcode,
+                                             DevStatus* st, unsigned& err) {
+    constexpr int R = (B == 4) ? 2 : 3;
+    constexpr int NJ = R * R * R;
+    const int lane = threadIdx.x & 31;
+    const unsigned FULL = 0xffffffffu;
+    const unsigned peers = __match_any_sync(FULL, t.key0);
     const int leader = __ffs(peers) - 1;
     const int rank = __popc(peers & ((1u << lane) - 1u));
     const int gsize = __popc(peers);
     unsigned gneed = 0;
     if (peers == FULL) {
-        gneed = __reduce_or_sync(FULL, need);   // the usual case: one group per warp
+        gneed = __reduce_or_sync(FULL, t.need);   // the usual case: one group per warp
     } else {
 #pragma unroll
         for (int j = 0; j < NJ; ++j)
-            if (__ballot_sync(FULL, (need >> j) & 1u) & peers) gneed |= 1u << j;
+            if (__ballot_sync(FULL, (t.need >> j) & 1u) & peers) gneed |= 1u << j;
     }
     int myslot = -1;
-    if (ok) {
+    if (t.ok) {
         // member `rank` takes block offsets rank, rank + gsize, ...
         for (int j = rank; j < NJ; j += gsize) {
             if (!((gneed >> j) & 1u)) continue;
-            const int bi = b0[0] + j / (R * R), bj = b0[1] + (j / R) % R, bk = b0[2] + j % R;
-            int slot;
-            if (SCAN) {
-                const uint32_t rk = rel_key(P, bi, bj, bk), bit = 1u << (rk & 31u);
-                if (!(*((volatile uint32_t*)&bmask[rk >> 5]) & bit)) atomicOr(&bmask[rk >> 5], bit);
-                slot = (int)rk;
-            } else {
-                slot = hash_insert(hv, pack_key(bi, bj, bk), rel_key(P, bi, bj, bk), P.max_probe, akey, aslot, cap,
-                                   bmask, st, err);
-            }
+            const int slot = insert_block<B, SCAN>(P, hv, t.b0, j, akey, aslot, cap, bmask, st, err);
             if (j == 0) myslot = slot;   // offset 0 (the base block) is taken by rank 0 = the leader
         }
     }
-    const int slot0 = __shfl_sync(FULL, myslot, leader);
-    if (ok) {
-        const int cell = (base[0] & (B - 1)) + B * ((base[1] & (B - 1)) + B * (base[2] & (B - 1)));
-        pcode[p] = slot0 < 0 ? 0xffffffffu : (uint32_t)slot0 * (uint32_t)(B * B * B) + (uint32_t)cell;
-    }
+    write_code(pcode, p, t.ok, __shfl_sync(FULL, myslot, leader), t.cell, B * B * B);
 }
 
 #ifndef MPM_INSERT_PER_LANE
@@ -237,7 +264,12 @@ constexpr int INS_PL = MPM_INSERT_PER_LANE;   // particles per lane in the inser
 
 // Each warp takes 32 x INS_PL consecutive particles, p, p + 32, ... per
 // lane; all their coordinates are loaded before the first one's probes, so
-// the later loads overlap them.
+// the later loads overlap them.  With B = 4 and two particles per lane, when
+// each half of the warp is one group (the usual case, particles being
+// sorted) both halves probe in one phase: one OR reduction over all 64
+// particles when they share their base block, else lanes 0-7 take the first
+// half's offsets and lanes 16-23 the second's.  Otherwise each half is
+// inserted as one group after the other.
 template <int B, bool SCAN>
 __global__ void __launch_bounds__(256) k_insert(const float* __restrict__ ps, int64_t stride, int64_t n,
                                                 Params P, HashView hv, uint32_t* __restrict__ akey,
@@ -246,6 +278,7 @@ __global__ void __launch_bounds__(256) k_insert(const float* __restrict__ ps, in
                                                 DevStatus* st) {
     if (st->go == 0u) return;   // written by the clear before this kernel: uniform
     const int lane = threadIdx.x & 31;
+    const unsigned FULL = 0xffffffffu;
     const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * INS_PL + lane;
     float xs[INS_PL][3];
 #pragma unroll
@@ -253,9 +286,34 @@ __global__ void __launch_bounds__(256) k_insert(const float* __restrict__ ps, in
 #pragma unroll
         for (int a = 0; a < 3; ++a) xs[h][a] = (p0 + 32 * h < n) ? ps[(PX + a) * stride + p0 + 32 * h] : 0.f;
     unsigned err = 0u;
+    Stencil<B> t[INS_PL];
 #pragma unroll
-    for (int h = 0; h < INS_PL; ++h)
-        insert_particle<B, SCAN>(ps, stride, n, p0 + 32 * h, xs[h], P, hv, akey, aslot, cap, bmask, pcode, st, err);
+    for (int h = 0; h < INS_PL; ++h) t[h] = particle_stencil<B>(ps, stride, n, p0 + 32 * h, xs[h], P, err);
+    bool done = false;
+    if (B == 4 && INS_PL == 2) {
+        const unsigned pa = __match_any_sync(FULL, t[0].key0), pb = __match_any_sync(FULL, t[INS_PL - 1].key0);
+        if (pa == FULL && pb == FULL) {   // warp-uniform: each half is one group
+            const Stencil<B>& ta = t[0];
+            const Stencil<B>& tb = t[INS_PL - 1];
+            const bool same = ta.key0 == tb.key0;
+            const unsigned na = __reduce_or_sync(FULL, ta.need), nb = __reduce_or_sync(FULL, tb.need);
+            const bool second = lane >= 16;
+            const int j = lane & 15;
+            const unsigned gneed = same ? (na | nb) : (second ? nb : na);
+            int slot = -1;
+            if (j < 8 && !(same && second) && ((gneed >> j) & 1u))
+                slot = insert_block<B, SCAN>(P, hv, second ? tb.b0 : ta.b0, j, akey, aslot, cap, bmask, st, err);
+            const int sa = __shfl_sync(FULL, slot, 0), sb = __shfl_sync(FULL, slot, same ? 0 : 16);
+            write_code(pcode, p0, ta.ok, sa, ta.cell, B * B * B);
+            write_code(pcode, p0 + 32 * (INS_PL - 1), tb.ok, sb, tb.cell, B * B * B);
+            done = true;
+        }
+    }
+    if (!done) {
+#pragma unroll
+        for (int h = 0; h < INS_PL; ++h)
+            insert_group<B, SCAN>(t[h], p0 + 32 * h, P, hv, akey, aslot, cap, bmask, pcode, st, err);
+    }
     raise_errors(st, err);
 }
 
