@@ -176,3 +176,45 @@ def test_negative_coordinates_and_box_edges(oracle_mod, B, flags):
     assert np.abs(g["m"][ok] - m[idx]).max() <= 1e-6 * np.abs(m).max()
     assert np.abs(g["mv"][ok] - mv[idx]).max() <= 1e-6 * np.abs(mv).max()
     assert np.all(g["m"][~ok] == 0)
+
+
+@pytest.mark.parametrize("B", [1, 4])
+@pytest.mark.parametrize("flags", [0, mpm.SCAN_COMPACTION])
+def test_key_range_extremes(oracle_mod, B, flags):
+    """Eq. (key) packs a node or block index i as i + 2^20 in 21 bits, so the
+    valid range is [-2^20, 2^20 - 1].  A box in the corner at the top of that
+    range in x and at the bottom in y (h = 1): the active set is bit-exact and
+    P2G matches the oracle.  Positions lie on a 1/8 grid, which float32
+    represents exactly at this magnitude (24 significant bits)."""
+    top, bottom = (1 << 20) - 1, -(1 << 20)
+    lo, hi = (top - 40, bottom, -12), (top, bottom + 30, 17)
+    rng = np.random.default_rng(23)
+    n = 2000
+    x = np.empty((n, 3), np.float64)
+    for a in range(3):
+        # stencil base in [lo, hi - 2]: x/h in [lo + 0.5, hi - 0.5)
+        x[:, a] = lo[a] + 0.5 + rng.integers(0, int((hi[a] - lo[a] - 1) * 8), n) / 8.0
+    for a in range(3):   # the first and the last stencil base on every axis
+        x[a, a] = lo[a] + 0.5
+        x[3 + a, a] = hi[a] - 0.5 - 0.125
+    x32 = x.astype(np.float32)
+    assert np.array_equal(x32.astype(np.float64), x)
+    wl = W.Workload("key_range", lo, hi, 1.0, 1e-4, (0.0, 0.0, -9.81), W.NEOHOOKEAN, 1e4, 0.3, 1000.0, 30.0, 8.0,
+                    W.FLOOR_NONE, 0.0, 0.0, x32, block_size=B, wall_layers=0)
+    sim = mpm.Simulation(mpm.config_from_workload(wl, flags=flags), x32)
+    keys = _gpu_keys(sim)
+    o = oracle_for(wl)
+    assert np.array_equal(keys, eq_keys(o.active_blocks(x32)))
+    b = mpm.unpack_keys(keys)
+    assert b.min(0).tolist() == [lo[a] // B for a in range(3)]
+    assert b.max(0).tolist() == [hi[a] // B for a in range(3)]
+    sim.p2g()
+    g = sim.read_grid()
+    m, mv, f = o.p2g(x32)
+    from tests.helpers import sparse_node_coords
+    nodes = sparse_node_coords(keys, B)
+    ok = np.all((nodes >= np.array(lo)) & (nodes <= np.array(hi)), axis=1)
+    idx = o.node_index(nodes[ok])
+    assert np.abs(g["m"][ok] - m[idx]).max() <= 1e-6 * np.abs(m).max()
+    assert np.abs(g["mv"][ok] - mv[idx]).max() <= 1e-6 * np.abs(mv).max()
+    assert np.all(g["m"][~ok] == 0)
