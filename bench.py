@@ -532,6 +532,8 @@ def main():
                     help="launch shapes p2g_ctas_per_sm,g2p_threads,g2p_regs instead of the autotuner's choice")
     ap.add_argument("--compaction", default="hash", choices=["hash", "scan"],
                     help="active-set realisation: the hash (Sec. 4.3) or the scan (Sec. 4.2)")
+    ap.add_argument("--deterministic", action="store_true",
+                    help="MPM_DETERMINISTIC: fixed-order P2G reduction and (block, cell, id) order (bitwise reproducible)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -554,7 +556,8 @@ def main():
         wl.n * STATE_BYTES_PER_PARTICLE / 1e6, L2_BYTES // 10 ** 6)) if flush is None else "flushed between steps"
     stream = torch.cuda.current_stream()
 
-    cflags = mpm.SCAN_COMPACTION if args.compaction == "scan" else 0
+    mode = mpm.DETERMINISTIC if args.deterministic else 0
+    cflags = (mpm.SCAN_COMPACTION if args.compaction == "scan" else 0) | mode
     sim = mpm.Simulation.from_workload(wl, flags=cflags, stream=stream, device_inputs=True)
     for _ in range(args.warmup):
         sim.step(1)
@@ -591,7 +594,8 @@ def main():
         pass
     peak = float(peaks.get("hbm_gbs", 6400.0))
     achieved = alg_bytes / (phases[dom] * 1e-3) / 1e9
-    traffic = measured_traffic(wl.name, dom)
+    # the counters were taken in the fast mode; the deterministic P2G is another kernel
+    traffic = None if args.deterministic else measured_traffic(wl.name, dom)
 
     e2e = None
     if not args.no_e2e:
@@ -601,7 +605,7 @@ def main():
 
     dense = None
     if not args.no_dense and wl.scenario_counts is None:   # ensembles run on the sparse grid only
-        dsim = mpm.Simulation.from_workload(wl, flags=mpm.DENSE_GRID, stream=stream, device_inputs=True)
+        dsim = mpm.Simulation.from_workload(wl, flags=mpm.DENSE_GRID | mode, stream=stream, device_inputs=True)
         for _ in range(3):
             dsim.step(1)
         d_ms = time_steps(dsim, args.dense_steps, flush)
@@ -633,6 +637,7 @@ def main():
             "config": dict(wl.describe(), l2=l2_note, step_launch="one mpm_step call of K steps (CUDA graphs)"
                            if flush is None else "mpm_step(1) per step",
                            parallelism="replicas" if ws > 1 else "single GPU", compaction=args.compaction,
+                           mode="deterministic" if args.deterministic else "fast",
                            tuning={k: tuning[k] for k in ("p2g_ctas_per_sm", "g2p_threads", "g2p_regs")},
                            active_blocks=st["n_active_blocks"], particle_blocks=st["n_particle_blocks"]),
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -640,7 +645,7 @@ def main():
                          "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                          "alg_bytes_per_launch": alg_bytes, "kernel_ms": phases[dom]},
             "phases_ms": phases,
-            "alu_check": alu_check(wl, phases, (clk.summary() or {}).get("sm_mhz")),
+            "alu_check": None if args.deterministic else alu_check(wl, phases, (clk.summary() or {}).get("sm_mhz")),
             "cpu_baseline": cpu,
             "e2e": e2e,
             "dense_gpu": dense,
