@@ -180,6 +180,33 @@ def _ptr(a):
     return C.c_void_p(a.ctypes.data), 0
 
 
+def check_array(a, n: int, k: int, name: str, output: bool = False):
+    """An array crossing the boundary as n x k float32 values: a torch CUDA
+    tensor (float32, contiguous) or a numpy array.  Input numpy arrays are
+    converted to contiguous float32 (the converted array is returned and must
+    be kept alive until the call); output numpy arrays must already be
+    contiguous, writeable float32, since the library writes into them.  The
+    library reads or writes exactly n * k values, so any other size is an
+    error here rather than an access past the buffer there."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        import torch
+        if not a.is_cuda or a.dtype != torch.float32 or not a.is_contiguous():
+            raise ValueError("%s: a device tensor must be CUDA, float32 and contiguous" % name)
+        if a.numel() != n * k:
+            raise ValueError("%s: %d values, expected %d x %d" % (name, a.numel(), n, k))
+        return a
+    if output:
+        if not (isinstance(a, np.ndarray) and a.dtype == np.float32 and a.flags.c_contiguous and a.flags.writeable):
+            raise ValueError("%s: an output array must be a contiguous, writeable float32 numpy array" % name)
+    else:
+        a = np.ascontiguousarray(a, dtype=np.float32)
+    if a.size != n * k:
+        raise ValueError("%s: %d values, expected %d x %d" % (name, a.size, n, k))
+    return a
+
+
 class Simulation:
     """One mpm_ctx.  Inputs: numpy float32 arrays (host) or torch CUDA tensors."""
 
@@ -189,20 +216,25 @@ class Simulation:
         self._keep = []
         if terrain is not None:
             t = np.ascontiguousarray(terrain, dtype=np.float32)
+            if t.ndim != 2:
+                raise ValueError("terrain: a (ny, nx) height map, got shape %s" % (t.shape,))
             self._keep.append(t)
             cfg.terrain_height = t.ctypes.data_as(C.POINTER(C.c_float))
             cfg.terrain_ny, cfg.terrain_nx = t.shape
         self.cfg = cfg
+        if x is None:
+            raise ValueError("x is required")
         arrays = [x, v, C_, F, phi]
         on_dev = [hasattr(a, "data_ptr") for a in arrays if a is not None]
         if on_dev and any(on_dev) != all(on_dev):
             raise ValueError("mix of device and host inputs")
         device = bool(on_dev and on_dev[0])
+        n = int(x.shape[0]) if len(x.shape) else 0
+        arrays = [check_array(a, n, k, name) for a, k, name in
+                  zip(arrays, (3, 3, 9, 9, 1), ("x", "v", "C", "F", "phi"))]
         if not device:
-            arrays = [None if a is None else np.ascontiguousarray(a, dtype=np.float32) for a in arrays]
             self._keep.extend(a for a in arrays if a is not None)
         ptrs = [_ptr(a)[0] for a in arrays]
-        n = int(arrays[0].shape[0])
         self.n = n
         self._stream = stream
         sptr = None
@@ -256,17 +288,23 @@ class Simulation:
         if out is None:
             out = {"x": np.empty((self.n, 3), np.float32), "v": np.empty((self.n, 3), np.float32),
                    "C": np.empty((self.n, 3, 3), np.float32), "F": np.empty((self.n, 3, 3), np.float32)}
+        for key, k in (("x", 3), ("v", 3), ("C", 9), ("F", 9)):
+            check_array(out.get(key), self.n, k, key, output=True)
         ps = [_ptr(out.get(k)) for k in ("x", "v", "C", "F")]
         on_dev = [p[1] for p in ps if p[1] is not None]
+        if on_dev and any(on_dev) != all(on_dev):
+            raise ValueError("mix of device and host outputs")
         dev = 1 if (on_dev and on_dev[0]) else 0
         _check(lib().mpm_read_particles(self.h, *[p[0] for p in ps], dev), self.h)
         return out
 
     def write_particles(self, x=None, v=None, C_=None, F=None):
         arrs = [x, v, C_, F]
-        dev = any(hasattr(a, "data_ptr") for a in arrs if a is not None)
-        if not dev:
-            arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float32) for a in arrs]
+        on_dev = [hasattr(a, "data_ptr") for a in arrs if a is not None]
+        if on_dev and any(on_dev) != all(on_dev):
+            raise ValueError("mix of device and host inputs")
+        dev = bool(on_dev and on_dev[0])
+        arrs = [check_array(a, self.n, k, name) for a, k, name in zip(arrs, (3, 3, 9, 9), ("x", "v", "C", "F"))]
         ptrs = [_ptr(a)[0] for a in arrs]
         _check(lib().mpm_write_particles(self.h, *ptrs, 1 if dev else 0), self.h)
 
@@ -308,15 +346,28 @@ class Simulation:
     def state_bytes(self) -> int:
         return int(lib().mpm_state_bytes(self.h))
 
+    def _state_buffer(self, buf, name):
+        if not (hasattr(buf, "data_ptr") and buf.is_cuda and buf.is_contiguous()):
+            raise ValueError("%s: a contiguous CUDA tensor" % name)
+        if buf.numel() * buf.element_size() < self.state_bytes():
+            raise ValueError("%s: %d bytes, the state needs %d" % (name, buf.numel() * buf.element_size(),
+                                                                 self.state_bytes()))
+
     def save_state(self, dst):
+        self._state_buffer(dst, "dst")
         _check(lib().mpm_save_state(self.h, C.c_void_p(dst.data_ptr())), self.h)
 
     def load_state(self, src):
+        self._state_buffer(src, "src")
         _check(lib().mpm_load_state(self.h, C.c_void_p(src.data_ptr())), self.h)
 
     def adjoint_step(self, adj_next, adj_cur):
         """mpm_adjoint_step: adj_next, adj_cur are (n, 24) float32 CUDA tensors
         (x, v, C, F adjoints in id order); returns this step's (dL/dE, dL/dphi)."""
+        for a, name in ((adj_next, "adj_next"), (adj_cur, "adj_cur")):
+            if not hasattr(a, "data_ptr"):
+                raise ValueError("%s: a CUDA tensor" % name)
+            check_array(a, self.n, 24, name)
         dE, dphi = C.c_double(0.0), C.c_double(0.0)
         _check(lib().mpm_adjoint_step(self.h, C.c_void_p(adj_next.data_ptr()), C.c_void_p(adj_cur.data_ptr()),
                                       C.byref(dE), C.byref(dphi)), self.h)

@@ -3,6 +3,7 @@ and the bench's reporting helpers."""
 import math
 
 import numpy as np
+import pytest
 
 from paper_2605_28525_b300 import mpm, workloads as W
 
@@ -63,3 +64,42 @@ def test_bench_traffic_lookup_and_clock_summary(tmp_path):
     out = s.summary()
     assert out["sm_mhz"] == 1925.0 and out["sm_max_mhz"] == 2032.0 and out["reasons"] == ["sw_power_cap"]
     assert out["samples"] == 2 and abs(out["power_w_median"] - 705.25) < 1e-9
+
+
+def test_binding_rejects_arrays_of_the_wrong_size():
+    """Every array crossing the boundary holds exactly n x k float32 values:
+    anything else is refused in the binding, before the library could read or
+    write past the buffer."""
+    from paper_2605_28525_b300 import mpm
+    n = 10
+    ok = mpm.check_array(np.zeros((n, 3), np.float64), n, 3, "x")
+    assert ok.dtype == np.float32 and ok.flags.c_contiguous and ok.shape == (n, 3)
+    assert mpm.check_array(np.zeros((n, 3, 3)), n, 9, "F").size == n * 9
+    assert mpm.check_array(None, n, 3, "v") is None
+    for bad, k in ((np.zeros((n - 1, 3)), 3), (np.zeros((n, 2)), 3), (np.zeros(n * 3 + 1), 3), (np.zeros((n, 3, 2)), 9)):
+        with pytest.raises(ValueError):
+            mpm.check_array(bad, n, k, "a")
+    # outputs are written in place: no silent conversion
+    with pytest.raises(ValueError):
+        mpm.check_array(np.zeros((n, 3), np.float64), n, 3, "x", output=True)
+    with pytest.raises(ValueError):
+        mpm.check_array(np.zeros((3, n), np.float32).T, n, 3, "x", output=True)
+    ro = np.zeros((n, 3), np.float32)
+    ro.flags.writeable = False
+    with pytest.raises(ValueError):
+        mpm.check_array(ro, n, 3, "x", output=True)
+    assert mpm.check_array(np.zeros((n, 3), np.float32), n, 3, "x", output=True) is not None
+
+
+def test_binding_rejects_bad_inputs_before_creating_a_context():
+    from paper_2605_28525_b300 import mpm, workloads as W
+    wl = W.elastic_cube(steps=1)
+    cfg = mpm.config_from_workload(wl)
+    with pytest.raises(ValueError):
+        mpm.Simulation(cfg, wl.x, v=wl.v[:-1] if wl.v is not None else np.zeros((wl.n - 1, 3), np.float32))
+    with pytest.raises(ValueError):
+        mpm.Simulation(cfg, wl.x, F=np.zeros((wl.n, 4), np.float32))
+    with pytest.raises(ValueError):
+        mpm.Simulation(cfg, wl.x, phi=np.zeros(wl.n + 1, np.float32))
+    with pytest.raises(ValueError):
+        mpm.Simulation(cfg, wl.x, terrain=np.zeros(7, np.float32))
