@@ -137,6 +137,8 @@ def make_workload(name: str):
         return W.column_collapse()
     if name == "column_collapse_4M":
         return W.column_collapse(cells_xy=64)
+    if name == "column_collapse_127M":   # 362 x 362 x 128 cells: 134,189,056 particles, about 40 GB on the device
+        return W.column_collapse(cells_xy=362)
     if name == "landslide_8M":
         return W.landslide()
     if name == "elastic_cube_32k":

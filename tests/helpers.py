@@ -49,3 +49,13 @@ def small_blob(n=3000, seed=3, dx=1.0 / 32, lo=10, hi=20, box=32, material=W.NEO
     wl = W.Workload("blob", (0, 0, 0), (box, box, box), dx, dt, g, material, E, 0.3, 1000.0, 30.0, 8.0,
                     W.FLOOR_NONE, 0.0, 0.0, x, v=v, block_size=block_size)
     return wl, Cm, F
+
+
+def phi_index(keys, nodes):
+    """phi index of node tuples given the active block keys (Phi order, B = 4)."""
+    kb = eq_keys(np.asarray(nodes) // 4)
+    r = np.searchsorted(keys, kb)
+    assert np.all(keys[r] == kb)
+    nodes = np.asarray(nodes)
+    l = (nodes[:, 0] % 4) + 4 * ((nodes[:, 1] % 4) + 4 * (nodes[:, 2] % 4))
+    return r * 64 + l

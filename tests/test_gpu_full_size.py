@@ -16,18 +16,9 @@ import numpy as np
 import pytest
 
 from paper_2605_28525_b300 import mpm, workloads as W
-from tests.helpers import U32, eq_keys, oracle_for, sparse_node_coords
+from tests.helpers import U32, eq_keys, oracle_for, phi_index as _phi_index, sparse_node_coords
 
 pytestmark = pytest.mark.gpu
-
-
-def _phi_index(keys, nodes):
-    """phi index of node tuples given the active block keys (Phi order)."""
-    kb = eq_keys(nodes // 4)
-    r = np.searchsorted(keys, kb)
-    assert np.all(keys[r] == kb)
-    l = (nodes[:, 0] % 4) + 4 * ((nodes[:, 1] % 4) + 4 * (nodes[:, 2] % 4))
-    return r * 64 + l
 
 
 @pytest.mark.parametrize("name", ["column_collapse_1M", "landslide_8M"])
