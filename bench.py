@@ -139,6 +139,8 @@ def make_workload(name: str):
         return W.column_collapse(cells_xy=64)
     if name == "column_collapse_127M":   # 362 x 362 x 128 cells: 134,189,056 particles, about 40 GB on the device
         return W.column_collapse(cells_xy=362)
+    if name == "column_collapse_454M":   # 488 x 488 x 250 cells: 476,288,000 particles, about 140 GB on the device
+        return W.column_collapse(cells_xy=488, cells_z=250)
     if name == "landslide_8M":
         return W.landslide()
     if name == "elastic_cube_32k":
