@@ -89,3 +89,44 @@ def test_python_binding_raises_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(mpm, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(ImportError):
         mpm.lib()
+
+
+def test_null_arguments_are_invalid(native):
+    """Every entry point that takes a context answers MPM_ERR_INVALID_ARG to
+    a NULL one (and to a NULL required pointer) before touching the device,
+    so these run without a GPU."""
+    L, E = native.lib(), native.ERR_INVALID_ARG
+    i64 = C.c_int64()
+    t, s = native.Tuning(), native.Stats()
+    dE, dphi = C.c_double(), C.c_double()
+    buf = (C.c_float * 8)()
+    assert L.mpm_rebuild_active(None, C.byref(i64), C.byref(i64)) == E
+    assert L.mpm_p2g(None) == E
+    assert L.mpm_grid_update(None) == E
+    assert L.mpm_g2p(None) == E
+    assert L.mpm_step(None, 1) == E
+    assert L.mpm_read_particles(None, buf, None, None, None, 0) == E
+    assert L.mpm_write_particles(None, buf, None, None, None, 0) == E
+    assert L.mpm_read_active(None, None, 0, C.byref(i64)) == E
+    assert L.mpm_read_grid(None, None, None, None, None, 0) == E
+    assert L.mpm_get_stats(None, C.byref(s)) == E
+    assert L.mpm_autotune(None, 1, C.byref(t)) == E
+    assert L.mpm_get_tuning(None, C.byref(t)) == E
+    assert L.mpm_set_tuning(None, C.byref(t)) == E
+    assert L.mpm_save_state(None, C.cast(buf, C.c_void_p)) == E
+    assert L.mpm_load_state(None, C.cast(buf, C.c_void_p)) == E
+    assert L.mpm_adjoint_step(None, buf, buf, C.byref(dE), C.byref(dphi)) == E
+    assert L.mpm_state_bytes(None) == 0
+    L.mpm_destroy(None)   # no-op
+    # creation: NULL config, positions or output handle
+    cfg = native.default_config()
+    x = np.full((4, 3), 0.5, np.float32)
+    h = C.c_void_p()
+    xp = x.ctypes.data_as(C.c_void_p)
+    assert L.mpm_create(None, 4, xp, None, None, None, None, 0, None, C.byref(h)) == E
+    assert L.mpm_create(C.byref(cfg), 4, None, None, None, None, None, 0, None, C.byref(h)) == E
+    assert L.mpm_create(C.byref(cfg), 4, xp, None, None, None, None, 0, None, None) == E
+    counts = (C.c_int64 * 2)(2, 0)
+    assert L.mpm_create_ensemble(C.byref(cfg), 2, counts, xp, None, None, None, None, 0, None, C.byref(h)) == E
+    assert L.mpm_create_ensemble(C.byref(cfg), 0, None, xp, None, None, None, None, 0, None, C.byref(h)) == E
+    assert not h.value
