@@ -543,9 +543,10 @@ __global__ void __launch_bounds__(128) k_interleave(const uint32_t* __restrict__
                                                     const int* __restrict__ bstart, const int* __restrict__ bend,
                                                     const int* __restrict__ pblocks, const DevStatus* stc,
                                                     const int* __restrict__ cs, const int* __restrict__ tsum,
-                                                    int ntiles, int64_t cap, uint32_t* __restrict__ skey2,
-                                                    uint32_t* __restrict__ perm2, int* __restrict__ ccount,
-                                                    uint8_t* __restrict__ cperm) {
+                                                    int ntiles, int64_t cap, const float* __restrict__ ps,
+                                                    int64_t pstride, uint32_t* __restrict__ byid,
+                                                    uint32_t* __restrict__ skey2, uint32_t* __restrict__ perm2,
+                                                    int* __restrict__ ccount, uint8_t* __restrict__ cperm) {
     __shared__ unsigned char slot_cell[4][64];
     __shared__ int hist_all[4][64], hist_low[4][64];
     if (cta_aborted(stc)) return;
@@ -627,18 +628,38 @@ __global__ void __launch_bounds__(128) k_interleave(const uint32_t* __restrict__
         }
         ccount[(int64_t)r * 64 + lane] = cnt0;
         ccount[(int64_t)r * 64 + 32 + lane] = cnt1;
+        // Deterministic mode on the counting sort (ps given): the counting
+        // sort leaves a cell's particles in arrival order, so each lane puts
+        // its two cells' particles in id order first: particle j goes to slot
+        // lo + (number of the cell's particles with a smaller id) of byid.
+        const uint32_t* src = perm;
+        if (ps) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int lo = h ? lo1 : lo0, cnt = h ? cnt1 : cnt0;
+                for (int j = 0; j < cnt; ++j) {
+                    const uint32_t pj = perm[lo + j];
+                    const uint32_t idj = __float_as_uint(ps[PID * pstride + pj]);
+                    int rank = 0;
+                    for (int i = 0; i < cnt; ++i)
+                        rank += __float_as_uint(ps[PID * pstride + perm[lo + i]]) < idj ? 1 : 0;
+                    byid[lo + rank] = pj;
+                }
+            }
+            src = byid;   // each lane reads back only its own cells' slots
+        }
         int off = 0;
         for (int k = 0; k <= e - s; ++k) {   // no cell holds more than the block's particles
             const unsigned M0 = __ballot_sync(FULL, cnt0 > k), M1 = __ballot_sync(FULL, cnt1 > k);
             if ((M0 | M1) == 0u) break;
             if (cnt0 > k) {
                 const int pos = s + off + __popc(M0 & lt);
-                perm2[pos] = perm[lo0 + k];
+                perm2[pos] = src[lo0 + k];
                 skey2[pos] = base + cell0;
             }
             if (cnt1 > k) {
                 const int pos = s + off + __popc(M0) + __popc(M1 & lt);
-                perm2[pos] = perm[lo1 + k];
+                perm2[pos] = src[lo1 + k];
                 skey2[pos] = base + cell1;
             }
             off += __popc(M0) + __popc(M1);
@@ -1040,7 +1061,10 @@ cudaError_t launch_assign(mpm_ctx* c) {
     return cudaGetLastError();
 }
 
-bool counting_sort(const mpm_ctx* c) { return !c->dense && !c->det; }
+// The sparse grid sorts particles by counting sort, in deterministic mode too:
+// the interleave then puts each cell's particles in id order, so the order
+// is (block, cell, id) as the dense grid's radix sort by (key, id) gives.
+bool counting_sort(const mpm_ctx* c) { return !c->dense; }
 
 cudaError_t launch_particle_keys(mpm_ctx* c) {
     const float* ps = c->ps[c->cur];
@@ -1095,9 +1119,11 @@ cudaError_t launch_ranges(mpm_ctx* c, const uint32_t* skey) {
     ++c->launches;
     if (c->B == 4) {
         const int o = 1 - c->sorted_sel;
+        const bool by_id = cnt && c->det;   // deterministic mode: id order inside every cell
         k_interleave<<<148 * 8, 128, 0, c->ls>>>(skey, c->pval[c->sorted_sel], c->bstart, c->bend, c->pblocks, c->dstat,
-                                                cnt ? c->cs : nullptr, c->tsum, ntiles, cap, c->pkey[o], c->pval[o],
-                                                c->ccount, cnt ? c->cperm : nullptr);
+                                                cnt ? c->cs : nullptr, c->tsum, ntiles, cap,
+                                                by_id ? c->ps[c->cur] : nullptr, c->pstride, c->prank, c->pkey[o],
+                                                c->pval[o], c->ccount, (cnt && !c->det) ? c->cperm : nullptr);
         c->sorted_sel = o;
         ++c->launches;
     }

@@ -1021,7 +1021,7 @@ cudaError_t launch_p2g(mpm_ctx* c) {
         ++c->launches;
         return cudaGetLastError();
     }
-    const uint8_t* cp = counting_sort(c) ? c->cperm : nullptr;   // cells ordered by count (fast sparse mode)
+    const uint8_t* cp = (counting_sort(c) && !c->det) ? c->cperm : nullptr;   // cells ordered by count (fast sparse mode)
 #define MPM_CELLS(D_, T_)                                                                                         \
     k_p2g_cells<D_, T_><<<NUM_SMS * c->tune.p2g_ctas_per_sm, CellTileCfg::WARPS * 32, 0, c->ls>>>(ps, c->pstride, perm, c->bstart, c->bend, \
                                                                        c->pblocks, c->ccount, cp, c->dstat, c->P, \
