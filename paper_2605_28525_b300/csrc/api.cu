@@ -278,7 +278,7 @@ void update_live_cap(mpm_ctx* c) {
     int64_t live = c->dense ? c->n_dom_blocks : c->block_cap;
     live = std::min(live, c->brange_cap);
     live = std::min(live, c->node_cap / c->B3);
-    if (c->det) live = std::min<int64_t>(live, c->tbuf_cap / (7 * 216));
+    if (c->det) live = std::min<int64_t>(live, c->tbuf_cap / DET_TILE_FLOATS);
     c->live_cap = live;
     c->P.cap_blocks = (int)live;
 }
@@ -339,7 +339,7 @@ mpm_status do_rebuild(mpm_ctx* c) {
     const int64_t nodes = c->n_active * c->B3;
     CK(ensure_grid(c, nodes));
     CK(ensure_block_arrays(c, c->n_active));
-    if (c->det) CK(grow(c, c->tbuf, c->tbuf_cap, c->n_active * 7 * 216, 1.25));
+    if (c->det) CK(grow(c, c->tbuf, c->tbuf_cap, c->n_active * DET_TILE_FLOATS, 1.25));
     update_live_cap(c);
     CK(launch_assign(c));
     CK(launch_particle_keys(c));
@@ -456,7 +456,7 @@ mpm_status prepare_batch(mpm_ctx* c) {
     }
     CK(ensure_grid(c, want * c->B3));
     CK(ensure_block_arrays(c, want));
-    if (c->det) CK(grow(c, c->tbuf, c->tbuf_cap, want * 7 * 216, 1.25));
+    if (c->det) CK(grow(c, c->tbuf, c->tbuf_cap, want * DET_TILE_FLOATS, 1.25));
     update_live_cap(c);
     if (!(c->cfg.flags & MPM_NO_GRAPHS)) {
         for (int p = 0; p < 2; ++p)

@@ -270,6 +270,10 @@ struct RadixScratch {
 
 }  // namespace mpm
 
+// Deterministic mode: a block's two half-block partial tiles of 7 channels x
+// 216 nodes each, stored by P2G and summed in a fixed order by its reduce.
+constexpr int64_t DET_TILE_FLOATS = 2 * 7 * 216;
+
 struct mpm_ctx {
     mpm_config cfg;
     mpm::Params P;
@@ -316,7 +320,7 @@ struct mpm_ctx {
     int* cs = nullptr;           // counting sort: exclusive scan of bins (+ total)
     int* tsum = nullptr;         // counting sort: scan tile totals
     uint32_t* prank = nullptr;   // counting sort: rank of each particle in its bin
-    float* tbuf = nullptr;       // deterministic mode: 7 x 216 tile floats per block
+    float* tbuf = nullptr;       // deterministic mode: DET_TILE_FLOATS per block
     int64_t tbuf_cap = 0;
     int* hasp = nullptr;         // per Phi: generation (DevStatus.gen) of the last step the block held particles
 

@@ -179,13 +179,14 @@ __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, MPM_P2G_MINB) k_p2g_c
     const int* __restrict__ nbr, float4* __restrict__ gmv, float4* __restrict__ gf, float* __restrict__ tbuf,
     DevStatus* st) {
     using K = CellTileCfg;
-    // Work unit: half a block's cells in the fast mode, a whole block in the
-    // deterministic mode (its tile goes to tbuf as one piece).  Units are
-    // handed out dynamically.  Slot j (lane j % 32 of half j / 32) holds
-    // cell cperm[j] when the rebuild ordered the cells by count (the fast
-    // mode on the sparse grid: the units span the whole tile), else cell j
-    // (a half is then the z-layers 2h, 2h+1 and its tile layers 2h..2h+3).
-    constexpr int HU = DET ? 1 : 2;
+    // Work unit: half a block's cells, handed out dynamically (in the
+    // deterministic mode each half stores its whole tile to tbuf, zeros
+    // included, as one of the block's two partial tiles).  Slot j (lane
+    // j % 32 of half j / 32) holds cell cperm[j] when the rebuild ordered the
+    // cells by count (the fast mode on the sparse grid: the units span the
+    // whole tile), else cell j (a half is then the z-layers 2h, 2h+1 and, in
+    // the fast mode, its tile layers 2h..2h+3).
+    constexpr int HU = 2;
     const bool by_count = !DET && cperm != nullptr;
     const int TZ = (DET || by_count) ? K::T : 4;
     __shared__ float tiles[K::WARPS][7][K::TILE];
@@ -211,7 +212,7 @@ __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, MPM_P2G_MINB) k_p2g_c
         if (u >= nunits) break;
         const int r = pblocks[u / HU];
         if (!index_ok(r, P.cap_blocks, st)) continue;
-        const int h0 = DET ? 0 : u % HU, h1 = DET ? 2 : h0 + 1;
+        const int h0 = u % HU, h1 = h0 + 1;
         const int zoff = (DET || by_count) ? 0 : 2 * h0;   // block z-layer of the tile's layer 0
         const int s = bstart[r], kcap = bend[r] - s;   // no cell holds more than the block's particles
         const int cnt0 = ccount[(int64_t)r * 64 + lane], cnt1 = ccount[(int64_t)r * 64 + 32 + lane];
@@ -311,7 +312,7 @@ __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, MPM_P2G_MINB) k_p2g_c
                 tile[k][ti] = 0.f;
             }
             if (DET) {
-                float* T = tbuf + (int64_t)r * (7 * 216);
+                float* T = tbuf + ((int64_t)r * 2 + h0) * (7 * 216);
 #pragma unroll
                 for (int k = 0; k < 7; ++k) T[k * 216 + t] = v[k];
                 continue;
@@ -341,11 +342,11 @@ __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, MPM_P2G_MINB) k_p2g_c
 
 // --------------------------------------------- P2G: deterministic reduce
 
-// Deterministic mode: every block writes its finished tile (7 channels x
-// 216 nodes) to tbuf instead of adding it to the grid.  Each active node then
-// sums the tiles of the (at most 8) blocks b - e, e in {0,1}^3, that cover it,
-// in the fixed order e = 0..7 and only for blocks that hold particles this
-// step.  The result does not depend on thread timing, and the sparse and the
+// Deterministic mode: every half block writes its finished tile (7 channels
+// x 216 nodes) to tbuf instead of adding it to the grid.  Each active node
+// then sums the tiles of the (at most 8) blocks b - e, e in {0,1}^3, that
+// cover it, in the fixed order e = 0..7 and, for each, half 0 then half 1,
+// only for blocks that hold particles this step.  The result does not depend on thread timing, and the sparse and the
 // dense grid produce the same bits (absent blocks hold no particles).
 template <bool DENSE>
 __global__ void __launch_bounds__(256) k_p2g_reduce(int64_t cap, const DevStatus* st, Params P, HashView hv,
@@ -369,9 +370,12 @@ __global__ void __launch_bounds__(256) k_p2g_reduce(int64_t cap, const DevStatus
         const int rs = block_rank<DENSE>(P, hv, bc[0] - ex, bc[1] - ey, bc[2] - ez);
         if (rs < 0 || hasp[rs] != gen) continue;
         const int t = (lx + 4 * ex) + 6 * ((ly + 4 * ey) + 6 * (lz + 4 * ez));
-        const float* T = tbuf + (int64_t)rs * (7 * 216);
 #pragma unroll
-        for (int k = 0; k < 7; ++k) v[k] += T[k * 216 + t];
+        for (int h = 0; h < 2; ++h) {
+            const float* T = tbuf + ((int64_t)rs * 2 + h) * (7 * 216);
+#pragma unroll
+            for (int k = 0; k < 7; ++k) v[k] += T[k * 216 + t];
+        }
     }
     const float fs = -P.V0 * P.inv_h;
     gmv[i] = make_float4(v[0] * P.mp, v[1] * P.mp, v[2] * P.mp, v[3] * P.mp);
