@@ -212,8 +212,10 @@ class ClockSampler:
                    ("hw_thermal_slowdown", 0x40), ("hw_power_brake", 0x80))
 
     def _run_nvml(self, nv):
+        # at least one sample, also when a short timed region ends before the
+        # thread's first pass
         mx = nv.max_clock()
-        while not self._stop.is_set():
+        while True:
             sm = nv.clock()
             r = nv.reasons()
             try:
@@ -221,7 +223,8 @@ class ClockSampler:
             except Exception:
                 pw = None
             self.rows.append((float(sm), float(mx), pw, [n for n, m in self.REASON_BITS if r & m]))
-            self._stop.wait(0.002)
+            if self._stop.wait(0.002):
+                break
 
     def __enter__(self):
         import threading
