@@ -4,7 +4,10 @@ The mistakes are the plausible ones for this method: a flipped sign of the
 APIC affine term, a transposed C_p, a dropped gravity term, a wrong B-spline
 branch, a flipped internal-force sign, F updated on the wrong side, ln J
 replaced by J - 1, a wrong Drucker-Prager cone factor, a transposed APIC B_p,
-and a j-major block scan.  Each mutant is compiled to a temporary library and
+a j-major block scan, and four mistakes in the P2G rounding scales that set
+the GPU force tolerance (the particle volume without its 1/ppc, in both the
+dense and the node-query scale; the stress term dropped; the APIC term of the
+momentum scale dropped).  Each mutant is compiled to a temporary library and
 the pin suite is run against it in a subprocess.
 """
 import os
@@ -30,6 +33,14 @@ MUTANTS = {
                   "double dgamma = ndev + (3.0 * la + 2.0 * mu) / (3.0 * mu) * tr * alpha;"),
     "apic_B_transposed": ("Bm[3 * r + c] += w[q] * vn27[3 * q + r] * d[c];",
                           "Bm[3 * r + c] += w[q] * vn27[3 * q + c] * d[r];"),
+    "abs_force_volume_no_ppc": ("af[3 * id + r] += g1 * particle_volume(P) * (tmax + mu + la);",
+                                "af[3 * id + r] += g1 * P->h * P->h * P->h * (tmax + mu + la);"),
+    "abs_force_no_stress": ("af[3 * id + r] += g1 * particle_volume(P) * (tmax + mu + la);",
+                            "af[3 * id + r] += g1 * particle_volume(P) * (mu + la);"),
+    "abs_momentum_no_C": ("s += fabs(C[9 * p + 3 * r + c]) * fabs(nodes[3 * q + c] * P->h - x[3 * p + c]);",
+                          "s += 0.0;"),
+    "node_scale_volume_no_ppc": ("af[k] += (fabs(gw[3 * q]) + fabs(gw[3 * q + 1]) + fabs(gw[3 * q + 2])) * particle_volume(P) *",
+                                 "af[k] += (fabs(gw[3 * q]) + fabs(gw[3 * q + 1]) + fabs(gw[3 * q + 2])) * P->h * P->h * P->h *"),
     "scan_j_major": ("q = q * nb[ax] + (floordiv(n[ax], B) - blo[ax]);",
                      "q = q * nb[(ax + 1) % 3] + (floordiv(n[(ax + 1) % 3], B) - blo[(ax + 1) % 3]);"),
 }

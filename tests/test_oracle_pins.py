@@ -203,6 +203,92 @@ def test_p2g_no_mass_outside_active_blocks(oracle_mod):
     assert all(tuple(int(c) // 4 for c in n) in blocks for n in nodes)
 
 
+# ------------------------------------------- P2G rounding scales (A_n)
+#
+# orc_p2g_abs and the scale output of orc_p2g_nodes give, per node, sums of
+# absolute values that bound each P2G family: A^m = sum N m_p,
+# A^mv_r = sum N m_p (|v_r| + sum_c |C_rc| |x_n,c - x_p,c|) and
+# A^f = sum |grad N|_1 V0 (max|tau_p| + mu + lambda).  The GPU force check
+# multiplies A^f by a few ulps, so an inflated A^f would make that check
+# vacuous and a deflated one would make it fail for the wrong reason.  The
+# pins below fix A^f from both sides: a hand-computed value, the bound it must
+# satisfy, and its scaling with the particle volume.
+
+
+def _lame(E, nu):
+    """Textbook Lame constants of an isotropic solid."""
+    return E / (2 * (1 + nu)), E * nu / ((1 + nu) * (1 - 2 * nu))
+
+
+@pytest.mark.parametrize("s", [1.0, 1.2])
+def test_p2g_abs_one_particle_hand_value(oracle_mod, s):
+    """One particle at the centre of cell (10, 11, 12), F = s I (Neo-Hookean).
+
+    Per axis the stencil nodes sit at d = x/h - n = 1/2, -1/2, -3/2, where the
+    quadratic B-spline is 1/2, 1/2, 0 and its derivative -1, +1, 0.  So the 8
+    nodes {10, 11} x {11, 12} x {12, 13} carry N = 1/8 and
+    |grad N|_1 = 3 (1 * 1/2 * 1/2) / h = 3 / (4 h); the other 19 carry nothing.
+    tau = s I-stretch Neo-Hookean stress = (mu (s^2 - 1) + 3 lambda ln s) I.
+    Hence on those 8 nodes: A^f = 3/(4h) V0 (tau_ii + mu + lambda),
+    f_r = -V0 tau_ii dN/dx_r with |f_r| = V0 tau_ii / (4 h),
+    A^mv_r = m_p |v_r| / 8 (C = 0) and A^m = m_p / 8.
+    """
+    E, nu, h, ppc, rho = 1e5, 0.3, 1.0 / 32, 8.0, 1000.0
+    o = make(oracle_mod, E=E, nu=nu, h=h, ppc=ppc, rho=rho)
+    mu, la = _lame(E, nu)
+    V0, mp = h ** 3 / ppc, rho * h ** 3 / ppc
+    t = mu * (s * s - 1) + 3 * la * math.log(s)
+    x = np.array([[10.5, 11.5, 12.5]]) * h
+    v = np.array([[1.0, -2.0, 3.0]])
+    F = (s * np.eye(3)).reshape(1, 3, 3)
+    am, amv, af = o.p2g_abs(x, v, np.zeros((1, 3, 3)), F)
+    m, mv, f = o.p2g(x, v, np.zeros((1, 3, 3)), F)
+    corners = np.array([[i, j, k] for i in (10, 11) for j in (11, 12) for k in (12, 13)])
+    idx = o.node_index(corners)
+    want_af = 3.0 / (4.0 * h) * V0 * (t + mu + la)
+    assert np.allclose(af[idx], want_af, rtol=1e-13)
+    assert np.allclose(amv[idx], mp * np.abs(v[0]) / 8, rtol=1e-13)
+    assert np.allclose(am[idx], mp / 8, rtol=1e-13)
+    assert np.allclose(np.abs(f[idx]), V0 * t / (4 * h), rtol=1e-12, atol=1e-12 * want_af)
+    others = np.setdiff1d(np.flatnonzero(am), idx)
+    assert others.size == 0 and np.count_nonzero(af) == 8 * 3
+    # the node query's scale (one value per node) is the same sum
+    _, _, _, afn = o.p2g_nodes(corners, x, v, np.zeros((1, 3, 3)), F, with_scale=True)
+    assert np.allclose(afn, want_af, rtol=1e-13)
+
+
+@pytest.mark.parametrize("material", [0, 1])
+def test_p2g_abs_bounds_every_family(oracle_mod, material):
+    """|m_n| = A^m, |mv_n,r| <= A^mv_n,r and |f_n,r| <= A^f_n,r on every node,
+    for states whose stresses exceed mu + lambda and whose APIC term dominates."""
+    o = make(oracle_mod, material=material, phi_deg=30.0)
+    x, v, Cm, F = _random_state(400, 21, lo=10, hi=22)
+    rng = np.random.default_rng(22)
+    F = (1.6 * np.eye(3) + 0.2 * rng.standard_normal((len(x), 3, 3))).astype(np.float32)
+    v[: len(x) // 2] = 0.0                      # momentum from C alone on half the particles
+    am, amv, af = o.p2g_abs(x, v, Cm, F)
+    m, mv, f = o.p2g(x, v, Cm, F)
+    assert np.allclose(am, m, rtol=1e-14, atol=0)
+    assert np.all(np.abs(mv) <= amv * (1 + 1e-12))
+    assert np.all(np.abs(f) <= af * (1 + 1e-12))
+    # the bound is not vacuous: it is within a modest factor on the busiest nodes
+    busy = af[:, 0] > 0.5 * af[:, 0].max()
+    assert np.median((af / np.maximum(np.abs(f), 1e-300))[busy].min(1)) < 60
+    nodes = o.dense_nodes()[np.flatnonzero(m)[::17]]
+    _, _, fn, afn = o.p2g_nodes(nodes, x, v, Cm, F, with_scale=True)
+    assert np.all(np.abs(fn) <= afn[:, None] * (1 + 1e-12))
+    assert np.allclose(afn, af[o.node_index(nodes), 0], rtol=1e-12)
+
+
+def test_p2g_abs_scales_with_particle_volume(oracle_mod):
+    """V0 = m_p / rho = h^3 / ppc: halving ppc doubles every scale."""
+    x, v, Cm, F = _random_state(200, 23)
+    a8 = make(oracle_mod, ppc=8.0).p2g_abs(x, v, Cm, F)
+    a4 = make(oracle_mod, ppc=4.0).p2g_abs(x, v, Cm, F)
+    for s8, s4 in zip(a8, a4):
+        assert np.allclose(s4, 2 * s8, rtol=1e-13, atol=0)
+
+
 # ------------------------------------------------------- full-step pins
 
 def _blob(oracle_mod, n=400, seed=7):
