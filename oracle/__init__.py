@@ -51,17 +51,25 @@ NEOHOOKEAN, DRUCKER_PRAGER = 0, 1
 FLOOR_NONE, FLOOR_STICKY, FLOOR_SLIP, FLOOR_COULOMB = 0, 1, 2, 3
 
 
-def build(force: bool = False) -> str:
-    """Compile mpm_oracle.c into a shared library with gcc (idempotent)."""
-    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    stale = force or not os.path.exists(_LIB) or max(
-        os.path.getmtime(_SRC), os.path.getmtime(_HDR)) > os.path.getmtime(_LIB)
+# The all-core build of the same source (gcc -fopenmp): P2G into per-thread
+# grids added in thread order, grid update and G2P split over the threads.  It
+# is a timing baseline only; the parity reference is the serial build.
+_LIB_OMP = os.path.join(_HERE, "_build", "libmpm_oracle_omp.so")
+
+
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile mpm_oracle.c into a shared library with gcc (idempotent);
+    `openmp` builds the all-core variant beside the serial one."""
+    out = _LIB_OMP if openmp else _LIB
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    stale = force or not os.path.exists(out) or max(
+        os.path.getmtime(_SRC), os.path.getmtime(_HDR)) > os.path.getmtime(out)
     if stale:
-        tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+        tmp = out + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared"] +
+                              (["-fopenmp"] if openmp else []) + ["-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
 
 
 class Params(C.Structure):
@@ -78,33 +86,37 @@ class Params(C.Structure):
     ]
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        _lib = C.CDLL(_OVERRIDE if _OVERRIDE else build())
-        dp = C.POINTER(C.c_double)
-        ip = C.POINTER(C.c_int32)
-        P = C.POINTER(Params)
-        L = _lib
-        L.orc_weights.argtypes = [P, dp, ip, dp, dp]
-        L.orc_Dp.argtypes = [P, dp, dp]
-        L.orc_active_blocks.argtypes = [P, C.c_int64, dp, ip, C.c_int64]
-        L.orc_active_blocks.restype = C.c_int64
-        L.orc_kirchhoff.argtypes = [P, dp, C.c_double, dp]
-        L.orc_dp_project.argtypes = [P, dp, C.c_double, dp, C.POINTER(C.c_int)]
-        L.orc_svd3.argtypes = [dp, dp, dp, dp]
-        L.orc_p2g.argtypes = [P, C.c_int64, dp, dp, dp, dp, dp, dp, dp, dp]
-        L.orc_p2g_abs.argtypes = [P, C.c_int64, dp, dp, dp, dp, dp, dp, dp, dp]
-        L.orc_p2g_nodes.argtypes = [P, C.c_int64, dp, dp, dp, dp, dp, C.c_int64, ip, dp, dp, dp, dp]
-        L.orc_grid_update.argtypes = [P, dp, dp, dp, dp]
-        L.orc_grid_node.argtypes = [P, ip, C.c_double, dp, dp, dp]
-        L.orc_g2p_one.argtypes = [P, dp, C.c_double, dp, dp, dp, dp]
-        L.orc_g2p.argtypes = [P, C.c_int64, dp, dp, dp, dp, dp, dp]
-        L.orc_run.argtypes = [P, C.c_int64, dp, dp, dp, dp, dp, C.c_int32]
-    return _lib
+def lib(openmp: bool = False):
+    """The serial oracle library (the parity reference), or with `openmp` the
+    all-core build of the same source."""
+    if openmp not in _libs:
+        _libs[openmp] = _declare(C.CDLL(build(openmp=True) if openmp else (_OVERRIDE if _OVERRIDE else build())))
+    return _libs[openmp]
+
+
+def _declare(L):
+    dp = C.POINTER(C.c_double)
+    ip = C.POINTER(C.c_int32)
+    P = C.POINTER(Params)
+    L.orc_weights.argtypes = [P, dp, ip, dp, dp]
+    L.orc_Dp.argtypes = [P, dp, dp]
+    L.orc_active_blocks.argtypes = [P, C.c_int64, dp, ip, C.c_int64]
+    L.orc_active_blocks.restype = C.c_int64
+    L.orc_kirchhoff.argtypes = [P, dp, C.c_double, dp]
+    L.orc_dp_project.argtypes = [P, dp, C.c_double, dp, C.POINTER(C.c_int)]
+    L.orc_svd3.argtypes = [dp, dp, dp, dp]
+    L.orc_p2g.argtypes = [P, C.c_int64, dp, dp, dp, dp, dp, dp, dp, dp]
+    L.orc_p2g_abs.argtypes = [P, C.c_int64, dp, dp, dp, dp, dp, dp, dp, dp]
+    L.orc_p2g_nodes.argtypes = [P, C.c_int64, dp, dp, dp, dp, dp, C.c_int64, ip, dp, dp, dp, dp]
+    L.orc_grid_update.argtypes = [P, dp, dp, dp, dp]
+    L.orc_grid_node.argtypes = [P, ip, C.c_double, dp, dp, dp]
+    L.orc_g2p_one.argtypes = [P, dp, C.c_double, dp, dp, dp, dp]
+    L.orc_g2p.argtypes = [P, C.c_int64, dp, dp, dp, dp, dp, dp]
+    L.orc_run.argtypes = [P, C.c_int64, dp, dp, dp, dp, dp, C.c_int32]
+    return L
 
 
 def _d(a):
@@ -128,7 +140,8 @@ class Oracle:
     def __init__(self, *, lo, hi, h, dt, g=(0.0, 0.0, -9.81), B=4, material=NEOHOOKEAN,
                  E=1e6, nu=0.3, rho=1000.0, phi_deg=30.0, ppc=8.0,
                  floor_kind=FLOOR_NONE, floor_z=0.0, floor_mu=0.0,
-                 terrain=None, terrain_mu=0.0, wall_layers=2):
+                 terrain=None, terrain_mu=0.0, wall_layers=2, openmp=False):
+        self.openmp = bool(openmp)   # the all-core build (timing only)
         self.p = Params()
         self.p.lo[:] = [int(v) for v in lo]
         self.p.hi[:] = [int(v) for v in hi]
@@ -163,20 +176,20 @@ class Oracle:
         nodes = np.zeros((27, 3), np.int32)
         w = np.zeros(27)
         gw = np.zeros((27, 3))
-        lib().orc_weights(C.byref(self.p), _d(x), _i(nodes), _d(w), _d(gw))
+        lib(self.openmp).orc_weights(C.byref(self.p), _d(x), _i(nodes), _d(w), _d(gw))
         return nodes, w, gw
 
     def Dp(self, x):
         x = _f64(x, (3,))
         D = np.zeros((3, 3))
-        lib().orc_Dp(C.byref(self.p), _d(x), _d(D))
+        lib(self.openmp).orc_Dp(C.byref(self.p), _d(x), _d(D))
         return D
 
     def active_blocks(self, x):
         x = _f64(x, (-1, 3))
         cap = max(64, 27 * len(x))
         out = np.zeros((cap, 3), np.int32)
-        n = lib().orc_active_blocks(C.byref(self.p), len(x), _d(x), _i(out), cap)
+        n = lib(self.openmp).orc_active_blocks(C.byref(self.p), len(x), _d(x), _i(out), cap)
         if n < 0:
             raise ValueError("orc_active_blocks failed (%d)" % n)
         return out[:n].copy()
@@ -184,7 +197,7 @@ class Oracle:
     def kirchhoff(self, F, phi_deg=None):
         F = _f64(F, (3, 3))
         tau = np.zeros((3, 3))
-        rc = lib().orc_kirchhoff(C.byref(self.p), _d(F), float(self.p.phi_deg if phi_deg is None else phi_deg),
+        rc = lib(self.openmp).orc_kirchhoff(C.byref(self.p), _d(F), float(self.p.phi_deg if phi_deg is None else phi_deg),
                                  _d(tau))
         if rc:
             raise ValueError("invalid stress state")
@@ -194,7 +207,7 @@ class Oracle:
         F = _f64(F, (3, 3))
         out = np.zeros((3, 3))
         cs = C.c_int(-1)
-        rc = lib().orc_dp_project(C.byref(self.p), _d(F), float(self.p.phi_deg if phi_deg is None else phi_deg),
+        rc = lib(self.openmp).orc_dp_project(C.byref(self.p), _d(F), float(self.p.phi_deg if phi_deg is None else phi_deg),
                                   _d(out), C.byref(cs))
         if rc:
             raise ValueError("invalid state")
@@ -221,7 +234,7 @@ class Oracle:
         m = np.zeros(self.nnodes)
         mv = np.zeros((self.nnodes, 3))
         f = np.zeros((self.nnodes, 3))
-        rc = lib().orc_p2g(C.byref(self.p), n, _d(x), _d(v), _d(C_), _d(F),
+        rc = lib(self.openmp).orc_p2g(C.byref(self.p), n, _d(x), _d(v), _d(C_), _d(F),
                            _d(phi) if phi is not None else None, _d(m), _d(mv), _d(f))
         if rc:
             raise ValueError("orc_p2g failed (%d)" % rc)
@@ -232,7 +245,7 @@ class Oracle:
         am = np.zeros(self.nnodes)
         amv = np.zeros((self.nnodes, 3))
         af = np.zeros((self.nnodes, 3))
-        rc = lib().orc_p2g_abs(C.byref(self.p), n, _d(x), _d(v), _d(C_), _d(F),
+        rc = lib(self.openmp).orc_p2g_abs(C.byref(self.p), n, _d(x), _d(v), _d(C_), _d(F),
                                _d(phi) if phi is not None else None, _d(am), _d(amv), _d(af))
         if rc:
             raise ValueError("orc_p2g_abs failed (%d)" % rc)
@@ -245,7 +258,7 @@ class Oracle:
         mv = np.zeros((len(q), 3))
         f = np.zeros((len(q), 3))
         af = np.zeros(len(q))
-        rc = lib().orc_p2g_nodes(C.byref(self.p), n, _d(x), _d(v), _d(C_), _d(F),
+        rc = lib(self.openmp).orc_p2g_nodes(C.byref(self.p), n, _d(x), _d(v), _d(C_), _d(F),
                                  _d(phi) if phi is not None else None, len(q), _i(q), _d(m), _d(mv), _d(f),
                                  _d(af) if with_scale else None)
         if rc:
@@ -257,7 +270,7 @@ class Oracle:
         mv = _f64(mv, (-1, 3))
         f = _f64(f, (-1, 3))
         vn = np.zeros_like(mv)
-        lib().orc_grid_update(C.byref(self.p), _d(m), _d(mv), _d(f), _d(vn))
+        lib(self.openmp).orc_grid_update(C.byref(self.p), _d(m), _d(mv), _d(f), _d(vn))
         return vn
 
     def grid_node(self, n, m, mv, f):
@@ -265,7 +278,7 @@ class Oracle:
         mv = _f64(mv, (3,))
         f = _f64(f, (3,))
         out = np.zeros(3)
-        lib().orc_grid_node(C.byref(self.p), _i(n), float(m), _d(mv), _d(f), _d(out))
+        lib(self.openmp).orc_grid_node(C.byref(self.p), _i(n), float(m), _d(mv), _d(f), _d(out))
         return out
 
     def g2p_one(self, vn27, x, F, phi_deg=None):
@@ -274,7 +287,7 @@ class Oracle:
         v = np.zeros(3)
         C_ = np.zeros((3, 3))
         F = _f64(F, (3, 3)).copy()
-        rc = lib().orc_g2p_one(C.byref(self.p), _d(vn27), float(self.p.phi_deg if phi_deg is None else phi_deg),
+        rc = lib(self.openmp).orc_g2p_one(C.byref(self.p), _d(vn27), float(self.p.phi_deg if phi_deg is None else phi_deg),
                                _d(x), _d(v), _d(C_), _d(F))
         if rc:
             raise ValueError("orc_g2p_one failed (%d)" % rc)
@@ -284,7 +297,7 @@ class Oracle:
         n, x, v, C_, F, phi = self._state(x, v, C_, F, phi)
         x, v, C_, F = x.copy(), v.copy(), C_.copy(), F.copy()
         vn = _f64(vn, (-1, 3))
-        rc = lib().orc_g2p(C.byref(self.p), n, _d(vn), _d(x), _d(v), _d(C_), _d(F),
+        rc = lib(self.openmp).orc_g2p(C.byref(self.p), n, _d(vn), _d(x), _d(v), _d(C_), _d(F),
                            _d(phi) if phi is not None else None)
         if rc:
             raise ValueError("orc_g2p failed (%d)" % rc)
@@ -293,7 +306,7 @@ class Oracle:
     def run(self, x, v=None, C_=None, F=None, phi=None, nsteps=1):
         n, x, v, C_, F, phi = self._state(x, v, C_, F, phi)
         x, v, C_, F = x.copy(), v.copy(), C_.copy(), F.copy()
-        rc = lib().orc_run(C.byref(self.p), n, _d(x), _d(v), _d(C_), _d(F),
+        rc = lib(self.openmp).orc_run(C.byref(self.p), n, _d(x), _d(v), _d(C_), _d(F),
                            _d(phi) if phi is not None else None, int(nsteps))
         if rc:
             raise ValueError("orc_run failed (%d)" % rc)

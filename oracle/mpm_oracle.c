@@ -31,6 +31,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* ------------------------------------------------------------------ helpers */
 
@@ -419,6 +422,66 @@ static double phi_of(const orc_params* P, const double* phi, int64_t p) {
     return phi ? phi[p] : P->phi_deg;
 }
 
+#ifdef _OPENMP
+/* The all-core build (gcc -fopenmp; a timing baseline only, never the parity
+ * reference): each thread scatters a contiguous share of the particles into
+ * its own dense grid, and the grids are added node by node in thread order,
+ * so a run is reproducible for a given thread count.  The serial build above
+ * is the one the tests check against. */
+static int p2g_threads(const orc_params* P, int64_t np, const double* x, const double* v,
+                       const double* C, const double* F, const double* phi, int64_t nn,
+                       double* m, double* mv, double* f) {
+    /* at most 16 GB of per-thread grids */
+    int nt = omp_get_max_threads();
+    const double grid_bytes = (double)nn * 7 * sizeof(double);
+    if (nt * grid_bytes > 16e9) nt = grid_bytes >= 16e9 ? 1 : (int)(16e9 / grid_bytes);
+    double* g = (double*)calloc((size_t)nt * (size_t)nn * 7, sizeof(double));
+    if (!g) return -4;
+    int rc = 0;
+#pragma omp parallel num_threads(nt) reduction(min : rc)
+    {
+        const int t = omp_get_thread_num(), nth = omp_get_num_threads();
+        double* gm = g + (size_t)t * nn * 7;
+        double* gmv = gm + nn;
+        double* gf = gmv + 3 * nn;
+        const int64_t p0 = np * t / nth, p1 = np * (t + 1) / nth;
+        int err = 0;
+        for (int64_t p = p0; p < p1 && err == 0; ++p) {
+            int32_t nodes[81];
+            double dm[27], dmv[81], df[81];
+            err = p2g_particle(P, &x[3 * p], &v[3 * p], &C[9 * p], &F[9 * p], phi_of(P, phi, p),
+                               nodes, dm, dmv, df);
+            for (int q = 0; q < 27 && err == 0; ++q) {
+                int64_t id = node_index(P, &nodes[3 * q]);
+                if (id < 0) {
+                    err = -1;
+                    break;
+                }
+                gm[id] += dm[q];
+                for (int a = 0; a < 3; ++a) {
+                    gmv[3 * id + a] += dmv[3 * q + a];
+                    gf[3 * id + a] += df[3 * q + a];
+                }
+            }
+        }
+        rc = err;
+#pragma omp barrier
+#pragma omp for schedule(static)
+        for (int64_t id = 0; id < nn; ++id)
+            for (int s = 0; s < nt; ++s) {
+                const double* sm = g + (size_t)s * nn * 7;
+                m[id] += sm[id];
+                for (int a = 0; a < 3; ++a) {
+                    mv[3 * id + a] += sm[nn + 3 * id + a];
+                    f[3 * id + a] += sm[4 * nn + 3 * id + a];
+                }
+            }
+    }
+    free(g);
+    return rc;
+}
+#endif
+
 int orc_p2g(const orc_params* P, int64_t np, const double* x, const double* v,
             const double* C, const double* F, const double* phi,
             double* m, double* mv, double* f) {
@@ -428,6 +491,9 @@ int orc_p2g(const orc_params* P, int64_t np, const double* x, const double* v,
     memset(m, 0, (size_t)nn * sizeof(double));
     memset(mv, 0, (size_t)nn * 3 * sizeof(double));
     memset(f, 0, (size_t)nn * 3 * sizeof(double));
+#ifdef _OPENMP
+    if (omp_get_max_threads() > 1) return p2g_threads(P, np, x, v, C, F, phi, nn, m, mv, f);
+#endif
     for (int64_t p = 0; p < np; ++p) {
         int32_t nodes[81];
         double dm[27], dmv[81], df[81];
@@ -608,6 +674,9 @@ void orc_grid_update(const orc_params* P, const double* m, const double* mv, con
                      double* vn) {
     int64_t d[3];
     box_dims(P, d);
+#ifdef _OPENMP
+#pragma omp parallel for collapse(2) schedule(static)
+#endif
     for (int64_t i = 0; i < d[0]; ++i)
         for (int64_t j = 0; j < d[1]; ++j)
             for (int64_t k = 0; k < d[2]; ++k) {
@@ -667,6 +736,27 @@ int orc_g2p_one(const orc_params* P, const double vn27[81], double phi_deg, doub
 
 int orc_g2p(const orc_params* P, int64_t np, const double* vn, double* x, double* v,
             double* C, double* F, const double* phi) {
+#ifdef _OPENMP
+    if (omp_get_max_threads() > 1) {
+        int rc = 0;
+#pragma omp parallel for schedule(static) reduction(min : rc)
+        for (int64_t p = 0; p < np; ++p) {
+            int32_t nodes[81];
+            double w[27], gw[81], v27[81];
+            orc_weights(P, &x[3 * p], nodes, w, gw);
+            int e = 0;
+            for (int q = 0; q < 27 && !e; ++q) {
+                int64_t id = node_index(P, &nodes[3 * q]);
+                if (id < 0) e = -1;
+                else
+                    for (int a = 0; a < 3; ++a) v27[3 * q + a] = vn[3 * id + a];
+            }
+            if (!e) e = orc_g2p_one(P, v27, phi_of(P, phi, p), &x[3 * p], &v[3 * p], &C[9 * p], &F[9 * p]);
+            if (e < rc) rc = e;
+        }
+        return rc;
+    }
+#endif
     for (int64_t p = 0; p < np; ++p) {
         int32_t nodes[81];
         double w[27], gw[81], v27[81];

@@ -582,14 +582,14 @@ __global__ void __launch_bounds__(128) k_adj_g2p(const float* __restrict__ ps, i
     double phi_part = 0.0;
     if (i < n) {
     const int64_t p = perm[i];
-    const int64_t id = (int64_t)__float_as_uint(ps[PID * stride + p]);
+    const int64_t id = (int64_t)__float_as_uint(ps[pel(p, PID)]);
     int q[8];
     block_neighbours<DENSE>(P, nbr, (int)(skey[i] >> 6), q);
     float x[3], F[9];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) x[k] = ps[(PX + k) * stride + p];
+    for (int k = 0; k < 3; ++k) x[k] = ps[pel(p, PX + k)];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) F[k] = ps[(PF + k) * stride + p];
+    for (int k = 0; k < 9; ++k) F[k] = ps[pel(p, PF + k)];
     float d[3], w[3][3], dw[3][3];
     int loc[3];
     particle_geometry(P, x, d, loc, w, dw);
@@ -631,7 +631,7 @@ __global__ void __launch_bounds__(128) k_adj_g2p(const float* __restrict__ ps, i
                 Ftr[r * 3 + s] = v;
             }
         double abar = 0.0;
-        const double alpha = (double)ps[PPHI * stride + p];
+        const double alpha = (double)ps[pel(p, PPHI)];
         if (dp_map_adjoint_series(Ftr, (float)alpha, (float)kappa, Fb_n, Fbt, &abar) ||
             dp_map_adjoint(Ftr, alpha, kappa, Fb_n, Fbt, &abar)) {
 #pragma unroll
@@ -845,22 +845,22 @@ __global__ void __launch_bounds__(128) k_adj_p2g(const float* __restrict__ ps, i
     double e_part = 0.0;
     if (i < n) {
         const int64_t p = perm[i];
-        const int64_t id = (int64_t)__float_as_uint(ps[PID * stride + p]);
+        const int64_t id = (int64_t)__float_as_uint(ps[pel(p, PID)]);
         int q[8];
         block_neighbours<DENSE>(P, nbr, (int)(skey[i] >> 6), q);
         float x[3], v[3], C[9], F[9], t6[6];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            x[k] = ps[(PX + k) * stride + p];
-            v[k] = ps[(PV + k) * stride + p];
+            x[k] = ps[pel(p, PX + k)];
+            v[k] = ps[pel(p, PV + k)];
         }
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
-            C[k] = ps[(PC + k) * stride + p];
-            F[k] = ps[(PF + k) * stride + p];
+            C[k] = ps[pel(p, PC + k)];
+            F[k] = ps[pel(p, PF + k)];
         }
 #pragma unroll
-        for (int k = 0; k < 6; ++k) t6[k] = ps[(PT + k) * stride + p];
+        for (int k = 0; k < 6; ++k) t6[k] = ps[pel(p, PT + k)];
         const float tau[9] = {t6[0], t6[1], t6[2], t6[1], t6[3], t6[4], t6[2], t6[4], t6[5]};
         float d[3], w[3][3], dw[3][3];
         int loc[3];

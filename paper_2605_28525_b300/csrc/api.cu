@@ -95,7 +95,7 @@ __global__ void k_load_comp(const float* __restrict__ src, int ncomp, int64_t n,
         float v;
         if (src) v = src[p * ncomp + k];
         else v = (identity_fill && (k % 4) == 0) ? 1.f : 0.f;
-        ps[(comp0 + k) * stride + p] = v;
+        ps[pel(p, comp0 + k)] = v;
     }
 }
 
@@ -107,24 +107,24 @@ __global__ void k_load_alpha(const float* __restrict__ phi, float phi_const, int
     // kept per particle so the step needs no trigonometry.
     const float ph = phi ? phi[p] : phi_const;
     const float sp = sinf(ph * 0.017453292519943295f);
-    ps[PPHI * stride + p] = 0.816496580927726f * 2.f * sp / (3.f - sp);
-    ps[PID * stride + p] = __uint_as_float((uint32_t)p);
+    ps[pel(p, PPHI)] = 0.816496580927726f * 2.f * sp / (3.f - sp);
+    ps[pel(p, PID)] = __uint_as_float((uint32_t)p);
 }
 
 __global__ void k_store_comp(const float* __restrict__ ps, int64_t stride, int64_t n, int comp0, int ncomp,
                              float* __restrict__ dst) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const int64_t id = (int64_t)__float_as_uint(ps[PID * stride + i]);
-    for (int k = 0; k < ncomp; ++k) dst[id * ncomp + k] = ps[(comp0 + k) * stride + i];
+    const int64_t id = (int64_t)__float_as_uint(ps[pel(i, PID)]);
+    for (int k = 0; k < ncomp; ++k) dst[id * ncomp + k] = ps[pel(i, comp0 + k)];
 }
 
 // Permute the whole state into id order (restart path).
 __global__ void k_to_id_order(const float* __restrict__ ps, float* __restrict__ po, int64_t stride, int64_t n) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const int64_t id = (int64_t)__float_as_uint(ps[PID * stride + i]);
-    for (int k = 0; k < NF; ++k) po[k * stride + id] = ps[k * stride + i];
+    const int64_t id = (int64_t)__float_as_uint(ps[pel(i, PID)]);
+    for (int k = 0; k < NF; ++k) po[pel(id, k)] = ps[pel(i, k)];
 }
 
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }

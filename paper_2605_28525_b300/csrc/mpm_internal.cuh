@@ -1,13 +1,20 @@
 // Internal declarations of the sparse-grid MPM library (sm_103a).
 //
 // Data layout in HBM (one context):
-//   particle state   two buffers (ping-pong), each structure-of-arrays with
-//                    NF float components of `pstride` entries: x(3) v(3)
-//                    C(9, row-major) F(9) tau(6, symmetric Kirchhoff stress
-//                    xx xy xz yy yz zz) alpha(1, Drucker-Prager cone constant
-//                    from the friction angle) id(1, uint32 bits).
-//                    G2P reads buffer `cur` through the sort permutation and
-//                    writes buffer 1-cur in sorted (block, cell) order.
+//   particle state   two buffers (ping-pong) of NF = 32 floats per particle:
+//                    x(3) alpha(1, Drucker-Prager cone constant from the
+//                    friction angle) F(9, row-major) id(1, uint32 bits)
+//                    tau(6, symmetric Kirchhoff stress xx xy xz yy yz zz)
+//                    v(3) C(9, row-major), i.e. 8 planes of 4 floats, stored
+//                    in tiles of 32 particles: tile p/32 holds its 8 planes
+//                    one after the other, each plane 32 float4 in particle
+//                    order (see pel).  A particle's planes lie 512 B apart
+//                    from one address, and one plane of 32 consecutive
+//                    particles is one 512 B run.  G2P reads planes 0-3 (x,
+//                    alpha, F, id) and writes all 8; P2G reads planes 0, 5-7
+//                    (x, v, C) and 0, 3-4 (x, tau).  G2P reads buffer `cur`
+//                    through the sort permutation and writes buffer 1-cur in
+//                    sorted (block, cell) order.
 //   hash table       H slots of uint64 keys (EMPTY = all ones) and int32
 //                    values = compact block index Phi (Sec. 4.3, Alg. 5-6).
 //   active list      block_cap entries of (relative block key, slot), sorted
@@ -25,10 +32,23 @@
 
 namespace mpm {
 
-// particle-state component offsets (in units of pstride)
+// particle-state components (their order fixes the planes: plane = k / 4)
 enum : int {
-    PX = 0, PV = 3, PC = 6, PF = 15, PT = 24, PPHI = 30, PID = 31, NF = 32
+    PX = 0, PPHI = 3, PF = 4, PID = 13, PT = 14, PV = 20, PC = 23, NF = 32
 };
+constexpr int NPLANE = NF / 4;
+
+// Float index of component k of the particle at storage index p: tile p / 32,
+// plane k / 4, lane p % 32, slot k % 4.  The buffers hold pstride (a multiple
+// of 32) particles.
+__host__ __device__ __forceinline__ int64_t pel(int64_t p, int k) {
+    return ((((p >> 5) * NPLANE + (k >> 2)) << 5) + (p & 31)) * 4 + (k & 3);
+}
+
+// float4 index of plane j of the particle at storage index p.
+__host__ __device__ __forceinline__ int64_t pel4(int64_t p, int j) {
+    return (((p >> 5) * NPLANE + j) << 5) + (p & 31);
+}
 
 constexpr uint64_t EMPTY_KEY = ~0ull;
 constexpr int KEY_BITS = 21;               // m of Eq. (key)
@@ -252,7 +272,7 @@ __device__ __forceinline__ void bspline_a(float d, int a, float& w, float& dw) {
 
 // CTAs of the P2G kernel that fit on one SM (registers and shared memory).
 #ifndef MPM_P2G_MAX_CTAS
-#define MPM_P2G_MAX_CTAS 4
+#define MPM_P2G_MAX_CTAS 3
 #endif
 
 // Launch shapes that change no result (mpm_autotune picks them).

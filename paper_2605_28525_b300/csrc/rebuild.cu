@@ -150,7 +150,8 @@ __device__ __forceinline__ bool particle_base_x(const float x[3], const Params& 
 
 __device__ __forceinline__ bool particle_base(const float* __restrict__ ps, int64_t stride, int64_t p,
                                               const Params& P, int base[3], unsigned& err) {
-    const float x[3] = {ps[(PX + 0) * stride + p], ps[(PX + 1) * stride + p], ps[(PX + 2) * stride + p]};
+    const float4 a0 = reinterpret_cast<const float4*>(ps)[pel4(p, 0)];
+    const float x[3] = {a0.x, a0.y, a0.z};
     return particle_base_x(x, P, base, err);
 }
 
@@ -189,7 +190,7 @@ __device__ __forceinline__ Stencil<B> particle_stencil(const float* __restrict__
             if (j / (R * R) < nbk[0] && (j / R) % R < nbk[1] && j % R < nbk[2]) t.need |= 1u << j;
     }
     // An ensemble's scenario s has its blocks ens_pitch * s further along x.
-    if (P.n_scen > 1 && t.ok) t.b0[0] += scenario_of(P, __float_as_uint(ps[PID * stride + p])) * P.ens_pitch;
+    if (P.n_scen > 1 && t.ok) t.b0[0] += scenario_of(P, __float_as_uint(ps[pel(p, PID)])) * P.ens_pitch;
     t.key0 = t.ok ? pack_key(t.b0[0], t.b0[1], t.b0[2]) : EMPTY_KEY;
     t.cell = (base[0] & (B - 1)) + B * ((base[1] & (B - 1)) + B * (base[2] & (B - 1)));
     return t;
@@ -282,9 +283,14 @@ __global__ void __launch_bounds__(256) k_insert(const float* __restrict__ ps, in
     const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * INS_PL + lane;
     float xs[INS_PL][3];
 #pragma unroll
-    for (int h = 0; h < INS_PL; ++h)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) xs[h][a] = (p0 + 32 * h < n) ? ps[(PX + a) * stride + p0 + 32 * h] : 0.f;
+    for (int h = 0; h < INS_PL; ++h) {
+        // plane 0 of the particle: x and alpha
+        const float4 a0 = (p0 + 32 * h < n) ? reinterpret_cast<const float4*>(ps)[pel4(p0 + 32 * h, 0)]
+                                             : make_float4(0.f, 0.f, 0.f, 0.f);
+        xs[h][0] = a0.x;
+        xs[h][1] = a0.y;
+        xs[h][2] = a0.z;
+    }
     unsigned err = 0u;
     Stencil<B> t[INS_PL];
 #pragma unroll
@@ -493,7 +499,7 @@ __global__ void k_particle_keys(const float* __restrict__ ps, int64_t stride, in
             k = (uint32_t)r * (uint32_t)B3 + code % (uint32_t)B3;
         }
     }
-    const int64_t q = by_id ? (int64_t)__float_as_uint(ps[PID * stride + p]) : p;
+    const int64_t q = by_id ? (int64_t)__float_as_uint(ps[pel(p, PID)]) : p;
     key[q] = k;
     val[q] = (uint32_t)p;
 }
@@ -639,10 +645,10 @@ __global__ void __launch_bounds__(128) k_interleave(const uint32_t* __restrict__
                 const int lo = h ? lo1 : lo0, cnt = h ? cnt1 : cnt0;
                 for (int j = 0; j < cnt; ++j) {
                     const uint32_t pj = perm[lo + j];
-                    const uint32_t idj = __float_as_uint(ps[PID * pstride + pj]);
+                    const uint32_t idj = __float_as_uint(ps[pel(pj, PID)]);
                     int rank = 0;
                     for (int i = 0; i < cnt; ++i)
-                        rank += __float_as_uint(ps[PID * pstride + perm[lo + i]]) < idj ? 1 : 0;
+                        rank += __float_as_uint(ps[pel(perm[lo + i], PID)]) < idj ? 1 : 0;
                     byid[lo + rank] = pj;
                 }
             }

@@ -14,9 +14,10 @@
 //   k_p2g_cells   one warp per half block (32 cells) that holds particles,
 //                 handed out dynamically, lane = cell, with
 //                 the block's particles in k-major order; register sums per
-//                 (cell, x-offset) and a warp-private shared tile updated
-//                 without atomics, flushed with float4 global atomics into the
-//                 active nodes.  Fast; the order of the global adds varies.
+//                 (cell, channel family) over the 27 stencil nodes and a
+//                 warp-private shared tile updated without atomics, flushed
+//                 with float4 global atomics into the active nodes.  Fast;
+//                 the order of the global adds varies.
 //   deterministic the same kernel with the block's particles in (cell, id)
 //                 order; each block stores its tile and k_p2g_reduce sums
 //                 the <= 8 tiles of every node in a fixed order: results are
@@ -63,15 +64,16 @@ __device__ __forceinline__ int block_rank(const Params& P, const HashView& hv, i
 // (cells in slot order) before the (k+1)-th particle of any cell; ccount
 // holds the particles per slot.  A warp takes a work unit of 32 slots (lane
 // l owns slot 32h + l of unit h; the rebuild orders the slots by count in the
-// fast sparse mode) with a private tile of (B+2)^3 = 216 nodes.  For each
-// (unit, x-offset a) pass the lanes walk k = 0, 1, ...: the k-th particles of
-// the 32 cells are consecutive in memory (coalesced loads), and each lane
-// accumulates its particle's 9 nodes (a, 0..2, 0..2) x 7 channels in
-// registers.  At the end of a pass the lanes hold distinct cells and the
-// same a, so for each node offset (b, c) their target nodes are distinct:
-// the tile is updated with plain read-modify-write, one warp-synchronised
-// step per offset, no atomics.  The finished tile is added to the active
-// nodes with float4 global atomics.
+// fast sparse mode) with a private tile of (B+2)^3 = 216 nodes.  The unit
+// runs two passes, momentum (m, m v) and force (f); in each the lanes walk
+// rounds k = 0, 1, ...: the k-th particles of the 32 cells are consecutive
+// in memory, and each lane sums its particle into the 27 nodes of its cell's
+// stencil in registers (108 momentum or 81 force accumulators).  A round's
+// particle planes are staged in shared memory by cp.async one round ahead.
+// At the end of a pass the lanes hold distinct cells, so for each node
+// offset their target nodes are distinct: the tile is updated with plain
+// read-modify-write, one warp-synchronised step per offset, no atomics.  The
+// finished tile is added to the active nodes with float4 global atomics.
 struct CellTileCfg {
     static constexpr int T = 6;                    // tile edge (B + 2 with B = 4)
     static constexpr int SY = 8, SZ = 52;          // strides: conflict-free for one half's 32 cells
@@ -80,27 +82,9 @@ struct CellTileCfg {
 };
 
 #ifndef MPM_P2G_MINB
-#define MPM_P2G_MINB 4
+#define MPM_P2G_MINB MPM_P2G_MAX_CTAS
 #endif
 
-// The P2G inputs of one particle: x, v, C (scaled by h) and tau.
-struct P2GIn {
-    float x[3], v[3], hc[9], t[6];
-    __device__ __forceinline__ void load(const float* __restrict__ ps, int64_t stride, int64_t p, float h) {
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            x[q] = ps[(PX + q) * stride + p];
-            v[q] = ps[(PV + q) * stride + p];
-        }
-#pragma unroll
-        for (int q = 0; q < 9; ++q) hc[q] = ps[(PC + q) * stride + p] * h;
-#pragma unroll
-        for (int q = 0; q < 6; ++q) t[q] = ps[(PT + q) * stride + p];
-    }
-};
-
-// Adds one particle's contributions to the 9 nodes (a, 0..2, 0..2) of its
-// stencil: 7 channels (m, m v, f) per node, in units of m_p and -V0/h.
 // The y and z B-spline weights of one particle together, in packed FP32
 // (d = (d_y, d_z)); the same formulas as bspline3.
 __device__ __forceinline__ void bspline3_yz(float2 d, float wy[3], float dwy[3], float wz[3], float dwz[3]) {
@@ -116,56 +100,113 @@ __device__ __forceinline__ void bspline3_yz(float2 d, float wy[3], float dwy[3],
     dwz[0] = -t0.y; dwz[1] = -2.f * t1.y; dwz[2] = t2.y;
 }
 
-// The 7 channels of one node, paired for Blackwell's packed FP32 pipes
-// (__ffma2_rn: two FMAs per instruction, each rounded as fmaf):
-// (m, m v_z), (m v_x, m v_y), (f_x, f_y), f_z.
-struct NodeAcc {
-    float2 m_mz, mxy, fxy;
-    float fz;
+// ---- two channel passes: one pass per channel family over all 27 stencil
+// nodes, so that each particle is loaded and its weights computed twice per
+// work unit, and the per-particle work is mostly the node sums themselves.
+
+// Momentum pass: m and m v (APIC) at the 27 nodes, in units of m_p.  With
+// q0 = v - hC d, the momentum at node (a, b, c) is q0 + hC (a, b, c).
+struct MomAcc {
+    float2 m_mz, mxy;
 };
 
-__device__ __forceinline__ void p2g_accumulate(const Params& P, const P2GIn& in, int a, NodeAcc (&acc)[3][3]) {
-    float d[3];
+// The planes each pass reads: 0 (x), 5 (v, C0), 6 (C1..C4), 7 (C5..C8) for
+// the momentum; 0 (x), 3 (F8, id, tau xx, xy), 4 (tau xz, yy, yz, zz) for
+// the force.
+__constant__ int kMomPlanes[4] = {0, 5, 6, 7};
+__constant__ int kForcePlanes[4] = {0, 3, 4, 0};
+
+__device__ __forceinline__ void p2g_momentum(const Params& P, const float4 (&pl)[4], MomAcc (&acc)[27]) {
+    const float4 a0 = pl[0], a5 = pl[1], a6 = pl[2], a7 = pl[3];
+    const float xs[3] = {a0.x, a0.y, a0.z};
+    const float v[3] = {a5.x, a5.y, a5.z};
+    const float cs[9] = {a5.w, a6.x, a6.y, a6.z, a6.w, a7.x, a7.y, a7.z, a7.w};
+    float d[3], hc[9];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-        const float fx = in.x[q] * P.inv_h;
+        const float fx = xs[q] * P.inv_h;
         d[q] = fx - (float)base_index(fx);      // exact
     }
-    const float* hc = in.hc;
-    const float* t = in.t;
-    float wx, dwx, wy[3], dwy[3], wz[3], dwz[3];
-    bspline_a(d[0], a, wx, dwx);
-    bspline3_yz(make_float2(d[1], d[2]), wy, dwy, wz, dwz);
-    // momentum at node (a, b, c): v + hC (a - dx, b - dy, c - dz)
-    const float ox = (float)a - d[0];
-    const float q0x = fmaf(hc[0], ox, in.v[0]) - hc[1] * d[1] - hc[2] * d[2];
-    const float q0y = fmaf(hc[3], ox, in.v[1]) - hc[4] * d[1] - hc[5] * d[2];
-    const float q0z = fmaf(hc[6], ox, in.v[2]) - hc[7] * d[1] - hc[8] * d[2];
-    const float2 hc25 = make_float2(hc[2], hc[5]);
-    const float2 t01 = make_float2(t[0], t[1]), t13 = make_float2(t[1], t[3]), t24 = make_float2(t[2], t[4]);
 #pragma unroll
-    for (int b = 0; b < 3; ++b) {
-        // tau . grad N over c: wz (tau_r0 dwx wy + tau_r1 wx dwy) + dwz tau_r2 wx wy
-        const float Pw = wx * wy[b], Gx = dwx * wy[b], Gy = wx * dwy[b];
-        const float2 A01 = __ffma2_rn(t01, make_float2(Gx, Gx), __fmul2_rn(t13, make_float2(Gy, Gy)));
-        const float2 B01 = __fmul2_rn(t24, make_float2(Pw, Pw));
-        const float A2 = fmaf(t[2], Gx, t[4] * Gy), B2 = t[5] * Pw;
-        const float2 qb = make_float2(fmaf(hc[1], (float)b, q0x), fmaf(hc[4], (float)b, q0y));
-        const float qbz = fmaf(hc[7], (float)b, q0z);
+    for (int q = 0; q < 9; ++q) hc[q] = cs[q] * P.h;
+    float wx[3], wy[3], wz[3], dw[3];
+    bspline3(d[0], wx, dw);
+    bspline3(d[1], wy, dw);
+    bspline3(d[2], wz, dw);
+    const float q0x = v[0] - hc[0] * d[0] - hc[1] * d[1] - hc[2] * d[2];
+    const float q0y = v[1] - hc[3] * d[0] - hc[4] * d[1] - hc[5] * d[2];
+    const float q0z = v[2] - hc[6] * d[0] - hc[7] * d[1] - hc[8] * d[2];
+    const float2 hx = make_float2(hc[0], hc[3]), hy = make_float2(hc[1], hc[4]), hz = make_float2(hc[2], hc[5]);
 #pragma unroll
-        for (int cc = 0; cc < 3; ++cc) {
-            const float N = Pw * wz[cc];
-            const float2 NN = make_float2(N, N);
-            const float2 mxy = __ffma2_rn(hc25, make_float2((float)cc, (float)cc), qb);
-            const float mz = fmaf(hc[8], (float)cc, qbz);
-            acc[b][cc].m_mz = __ffma2_rn(NN, make_float2(1.f, mz), acc[b][cc].m_mz);   // m: N x 1 + m, exact as N + m
-            acc[b][cc].mxy = __ffma2_rn(NN, mxy, acc[b][cc].mxy);
-            acc[b][cc].fxy = __ffma2_rn(make_float2(wz[cc], wz[cc]), A01,
-                                        __ffma2_rn(make_float2(dwz[cc], dwz[cc]), B01, acc[b][cc].fxy));
-            acc[b][cc].fz = fmaf(wz[cc], A2, fmaf(dwz[cc], B2, acc[b][cc].fz));
+    for (int a = 0; a < 3; ++a) {
+        const float2 qa = __ffma2_rn(hx, make_float2((float)a, (float)a), make_float2(q0x, q0y));
+        const float qaz = fmaf(hc[6], (float)a, q0z);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const float Pw = wx[a] * wy[b];
+            const float2 qb = __ffma2_rn(hy, make_float2((float)b, (float)b), qa);
+            const float qbz = fmaf(hc[7], (float)b, qaz);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float N = Pw * wz[c];
+                const float2 NN = make_float2(N, N);
+                const float2 qxy = __ffma2_rn(hz, make_float2((float)c, (float)c), qb);
+                const float qz = fmaf(hc[8], (float)c, qbz);
+                MomAcc& A = acc[(a * 3 + b) * 3 + c];
+                A.m_mz = __ffma2_rn(NN, make_float2(1.f, qz), A.m_mz);   // m: N x 1 + m, exact as N + m
+                A.mxy = __ffma2_rn(NN, qxy, A.mxy);
+            }
         }
     }
 }
+
+// Force pass: tau . grad N at the 27 nodes, in units of -V0/h.  For node
+// (a, b, c): f_r = wz (tau_r0 dwx wy + tau_r1 wx dwy) + dwz tau_r2 wx wy.
+struct ForceAcc {
+    float2 fxy;
+    float fz;
+};
+
+__device__ __forceinline__ void p2g_force(const Params& P, const float4 (&pl)[4], ForceAcc (&acc)[27]) {
+    const float4 a0 = pl[0], a3 = pl[1], a4 = pl[2];
+    const float xs[3] = {a0.x, a0.y, a0.z};
+    const float t[6] = {a3.z, a3.w, a4.x, a4.y, a4.z, a4.w};
+    float d[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const float fx = xs[q] * P.inv_h;
+        d[q] = fx - (float)base_index(fx);
+    }
+    float wx[3], dwx[3], wy[3], dwy[3], wz[3], dwz[3];
+    bspline3(d[0], wx, dwx);
+    bspline3_yz(make_float2(d[1], d[2]), wy, dwy, wz, dwz);
+    const float2 t01 = make_float2(t[0], t[1]), t13 = make_float2(t[1], t[3]), t24 = make_float2(t[2], t[4]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const float Pw = wx[a] * wy[b], Gx = dwx[a] * wy[b], Gy = wx[a] * dwy[b];
+            const float2 A01 = __ffma2_rn(t01, make_float2(Gx, Gx), __fmul2_rn(t13, make_float2(Gy, Gy)));
+            const float2 B01 = __fmul2_rn(t24, make_float2(Pw, Pw));
+            const float A2 = fmaf(t[2], Gx, t[4] * Gy), B2 = t[5] * Pw;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                ForceAcc& A = acc[(a * 3 + b) * 3 + c];
+                A.fxy = __ffma2_rn(make_float2(wz[c], wz[c]), A01,
+                                   __ffma2_rn(make_float2(dwz[c], dwz[c]), B01, A.fxy));
+                A.fz = fmaf(wz[c], A2, fmaf(dwz[c], B2, A.fz));
+            }
+        }
+}
+
+// 16-byte asynchronous copy global -> shared (L2 only), and its group fences.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 #ifndef MPM_P2G_PCACHE
 #define MPM_P2G_PCACHE 12   // rounds whose particle indices a lane loads once per work unit
@@ -193,6 +234,7 @@ __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, MPM_P2G_MINB) k_p2g_c
 #if MPM_P2G_PCACHE
     __shared__ uint32_t pcs[K::WARPS][MPM_P2G_PCACHE][32];   // the lanes' cached particle indices
 #endif
+    __shared__ __align__(16) float4 stage[K::WARPS][2][4][32];   // the lanes' staged particle planes, 2 rounds
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     float(&tile)[7][K::TILE] = tiles[wid];
     if (cta_aborted(stc)) return;
@@ -239,64 +281,117 @@ __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, MPM_P2G_MINB) k_p2g_c
                 __syncwarp();
             }
 #endif
-#pragma unroll 1
-            for (int a = 0; a < 3; ++a) {
-                NodeAcc acc[3][3];
-#pragma unroll
-                for (int b = 0; b < 3; ++b)
-#pragma unroll
-                    for (int cc = 0; cc < 3; ++cc) {
-                        acc[b][cc].m_mz = acc[b][cc].mxy = acc[b][cc].fxy = make_float2(0.f, 0.f);
-                        acc[b][cc].fz = 0.f;
-                    }
-                // round k: the k-th particle of every cell (both halves, in
-                // the block's k-major order)
-                int off = 0;
-                for (int k = 0;; ++k) {
-                    const unsigned M0 = __ballot_sync(FULL, cnt0 > k), M1 = __ballot_sync(FULL, cnt1 > k);
-                    if ((M0 | M1) == 0u) break;
-                    if (k >= kcap || off + __popc(M0) + __popc(M1) > kcap) {   // inconsistent counts
-                        miss |= 2u;
-                        break;
-                    }
-                    if (cnt > k) {
-                        uint32_t p;
-#if MPM_P2G_PCACHE
-                        if (k < MPM_P2G_PCACHE)
-                            p = pcs[wid][k][lane];
-                        else
-#endif
-                        {
-                            const int idx = h ? __popc(M0) + __popc(M1 & lt) : __popc(M0 & lt);
-                            p = perm[s + off + idx];
-                        }
-                        if (!index_ok(p, P.n_part, st)) continue;
-                        P2GIn in;
-                        in.load(ps, stride, p, P.h);
-                        p2g_accumulate(P, in, a, acc);
-                    }
-                    off += __popc(M0) + __popc(M1);
+            // Rounds of the unit: the fullest cell of this half.  Round k's
+            // particle of this lane: storage index and its offset in the
+            // block's k-major order; `nrun` particles of both halves precede
+            // round k + 1.  Each pass stages round k + 1's planes in the
+            // lane's half of the double buffer (cp.async) while round k is
+            // summed; every lane reads only its own staged planes.
+            const int R = __reduce_max_sync(FULL, cnt);
+            auto round_particle = [&](int k, int& off, uint32_t& p) -> bool {
+                const unsigned M0 = __ballot_sync(FULL, cnt0 > k), M1 = __ballot_sync(FULL, cnt1 > k);
+                const int nrun = __popc(M0) + __popc(M1);
+                bool ok = cnt > k;
+                if (k >= kcap || off + nrun > kcap) {   // inconsistent counts
+                    miss |= 2u;
+                    ok = false;
                 }
-                // For one node offset (b, c) the lanes' targets are distinct, but
-                // lane A's (b, c+1) target is lane B's (b, c) target when B's cell
-                // is one above A's: each offset is a separate warp-ordered step.
+                p = 0u;
+                if (ok) {
+#if MPM_P2G_PCACHE
+                    if (k < MPM_P2G_PCACHE)
+                        p = pcs[wid][k][lane];
+                    else
+#endif
+                        p = perm[s + off + (h ? __popc(M0) + __popc(M1 & lt) : __popc(M0 & lt))];
+                    ok = index_ok(p, P.n_part, st);
+                }
+                off += nrun;
+                return ok;
+            };
+            float4(&sbuf)[2][4][32] = stage[wid];
+            const float4* ps4 = reinterpret_cast<const float4*>(ps);
+            auto stage_planes = [&](bool ok, uint32_t p, int buf, const int* planes, int np) {
+                if (ok) {
+                    const float4* q4 = ps4 + pel4(p, 0);
 #pragma unroll
-                for (int b = 0; b < 3; ++b)
+                    for (int j = 0; j < 4; ++j)
+                        if (j < np) cp_async16(&sbuf[buf][j][lane], q4 + 32 * planes[j]);
+                }
+                cp_async_commit();
+            };
+            {
+                // momentum pass, then force pass: the lanes' 27-node sums of
+                // their cells, added to the tile one warp-ordered node offset
+                // at a time (for one offset the lanes' targets are distinct)
+                MomAcc macc[27];
 #pragma unroll
-                    for (int cc = 0; cc < 3; ++cc) {
-                        if (cnt > 0) {
-                            const int ti = (cx + a) + K::SY * (cy + b) + K::SZ * (cz + cc);
-                            const NodeAcc& q = acc[b][cc];
-                            tile[0][ti] += q.m_mz.x;
-                            tile[1][ti] += q.mxy.x;
-                            tile[2][ti] += q.mxy.y;
-                            tile[3][ti] += q.m_mz.y;
-                            tile[4][ti] += q.fxy.x;
-                            tile[5][ti] += q.fxy.y;
-                            tile[6][ti] += q.fz;
-                        }
-                        __syncwarp();
+                for (int q = 0; q < 27; ++q) macc[q].m_mz = macc[q].mxy = make_float2(0.f, 0.f);
+                int off = 0;
+                uint32_t p;
+                bool ok = round_particle(0, off, p);
+                stage_planes(ok && R > 0, p, 0, kMomPlanes, 4);
+#pragma unroll 1
+                for (int k = 0; k < R; ++k) {
+                    const bool cur = ok;
+                    if (k + 1 < R) ok = round_particle(k + 1, off, p);
+                    else ok = false;
+                    stage_planes(ok, p, (k + 1) & 1, kMomPlanes, 4);
+                    cp_async_wait1();
+                    if (cur) {
+                        const float4 pl[4] = {sbuf[k & 1][0][lane], sbuf[k & 1][1][lane], sbuf[k & 1][2][lane],
+                                              sbuf[k & 1][3][lane]};
+                        p2g_momentum(P, pl, macc);
                     }
+                }
+#pragma unroll
+                for (int q = 0; q < 27; ++q) {
+                    if (cnt > 0) {
+                        const int ti = (cx + q / 9) + K::SY * (cy + (q / 3) % 3) + K::SZ * (cz + q % 3);
+                        tile[0][ti] += macc[q].m_mz.x;
+                        tile[1][ti] += macc[q].mxy.x;
+                        tile[2][ti] += macc[q].mxy.y;
+                        tile[3][ti] += macc[q].m_mz.y;
+                    }
+                    __syncwarp();
+                }
+            }
+            {
+                ForceAcc facc[27];
+#pragma unroll
+                for (int q = 0; q < 27; ++q) {
+                    facc[q].fxy = make_float2(0.f, 0.f);
+                    facc[q].fz = 0.f;
+                }
+                cp_async_wait0();
+                int off = 0;
+                uint32_t p;
+                bool ok = round_particle(0, off, p);
+                stage_planes(ok && R > 0, p, 0, kForcePlanes, 3);
+#pragma unroll 1
+                for (int k = 0; k < R; ++k) {
+                    const bool cur = ok;
+                    if (k + 1 < R) ok = round_particle(k + 1, off, p);
+                    else ok = false;
+                    stage_planes(ok, p, (k + 1) & 1, kForcePlanes, 3);
+                    cp_async_wait1();
+                    if (cur) {
+                        const float4 pl[4] = {sbuf[k & 1][0][lane], sbuf[k & 1][1][lane], sbuf[k & 1][2][lane],
+                                              make_float4(0.f, 0.f, 0.f, 0.f)};
+                        p2g_force(P, pl, facc);
+                    }
+                }
+                cp_async_wait0();
+#pragma unroll
+                for (int q = 0; q < 27; ++q) {
+                    if (cnt > 0) {
+                        const int ti = (cx + q / 9) + K::SY * (cy + (q / 3) % 3) + K::SZ * (cz + q % 3);
+                        tile[4][ti] += facc[q].fxy.x;
+                        tile[5][ti] += facc[q].fxy.y;
+                        tile[6][ti] += facc[q].fz;
+                    }
+                    __syncwarp();
+                }
             }
         }
         // flush the tile: deterministic mode stores it for k_p2g_reduce, the
@@ -401,14 +496,14 @@ __global__ void __launch_bounds__(256) k_p2g_atomic(const float* __restrict__ ps
     float d[3], v[3], hc[9], t[6];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-        const float fx = ps[(PX + q) * stride + p] * P.inv_h;
+        const float fx = ps[pel(p, PX + q)] * P.inv_h;
         d[q] = fx - (float)base_index(fx);
-        v[q] = ps[(PV + q) * stride + p];
+        v[q] = ps[pel(p, PV + q)];
     }
 #pragma unroll
-    for (int q = 0; q < 9; ++q) hc[q] = ps[(PC + q) * stride + p] * P.h;
+    for (int q = 0; q < 9; ++q) hc[q] = ps[pel(p, PC + q)] * P.h;
 #pragma unroll
-    for (int q = 0; q < 6; ++q) t[q] = ps[(PT + q) * stride + p];
+    for (int q = 0; q < 6; ++q) t[q] = ps[pel(p, PT + q)];
     float wx[3], dwx[3], wy[3], dwy[3], wz[3], dwz[3];
     bspline3(d[0], wx, dwx);
     bspline3(d[1], wy, dwy);
@@ -837,12 +932,14 @@ __device__ __forceinline__ void g2p_particle(const float* __restrict__ ps, float
     constexpr int NC = B * B * B;
     Neighbours<B, DENSE> nb;
     nb.load(P, nbr, r);
+    // planes 0 (x, alpha), 1-2 (F0..F7), 3 (F8, id, tau xx, xy)
+    const float4* q4 = reinterpret_cast<const float4*>(ps) + pel4(p, 0);
+    const float4 a0 = q4[0];
     float d[3];
     int loc[3];
-    float xp[3];
+    const float xp[3] = {a0.x, a0.y, a0.z};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        xp[a] = ps[(PX + a) * stride + p];
         const float fx = xp[a] * P.inv_h;
         const int bi = base_index(fx);
         d[a] = fx - (float)bi;
@@ -915,25 +1012,28 @@ __device__ __forceinline__ void g2p_particle(const float* __restrict__ ps, float
     // for NaN or infinity.
     const float cs = 4.f * P.inv_h;
     const float ls = P.dt * P.inv_h;
+    float4* o4 = reinterpret_cast<float4*>(po) + pel4(i, 0);
     float sum = 0.f;
+    float xo[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const float xo = xp[a] + P.dt * vp[a];
-        sum += xo;
-        po[(PX + a) * stride + i] = xo;
-        po[(PV + a) * stride + i] = vp[a];
+        xo[a] = xp[a] + P.dt * vp[a];
+        sum += xo[a] + vp[a];
     }
+    float Cn[9];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const float c0 = cs * Bx[k], c1 = cs * By[k], c2 = cs * Bz[k];
-        sum += c0 + c1 + c2;
-        po[(PC + 3 * k + 0) * stride + i] = c0;
-        po[(PC + 3 * k + 1) * stride + i] = c1;
-        po[(PC + 3 * k + 2) * stride + i] = c2;
+        Cn[3 * k + 0] = cs * Bx[k];
+        Cn[3 * k + 1] = cs * By[k];
+        Cn[3 * k + 2] = cs * Bz[k];
+        sum += Cn[3 * k + 0] + Cn[3 * k + 1] + Cn[3 * k + 2];
     }
-    float F[9], Fn[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) F[k] = ps[(PF + k) * stride + p];
+    o4[0] = make_float4(xo[0], xo[1], xo[2], a0.w);
+    o4[5 * 32] = make_float4(vp[0], vp[1], vp[2], Cn[0]);
+    o4[6 * 32] = make_float4(Cn[1], Cn[2], Cn[3], Cn[4]);
+    o4[7 * 32] = make_float4(Cn[5], Cn[6], Cn[7], Cn[8]);
+    const float4 a1 = q4[32], a2 = q4[2 * 32], a3 = q4[3 * 32];
+    float F[9] = {a1.x, a1.y, a1.z, a1.w, a2.x, a2.y, a2.z, a2.w, a3.x}, Fn[9];
     const float L[9] = {Lx[0], Ly[0], Lz[0], Lx[1], Ly[1], Lz[1], Lx[2], Ly[2], Lz[2]};
 #pragma unroll
     for (int i2 = 0; i2 < 3; ++i2)
@@ -941,26 +1041,19 @@ __device__ __forceinline__ void g2p_particle(const float* __restrict__ ps, float
         for (int j2 = 0; j2 < 3; ++j2)
             Fn[i2 * 3 + j2] = F[i2 * 3 + j2] + ls * (L[i2 * 3 + 0] * F[0 * 3 + j2] + L[i2 * 3 + 1] * F[1 * 3 + j2] +
                                                     L[i2 * 3 + 2] * F[2 * 3 + j2]);
-    const float alpha = ps[PPHI * stride + p];
+    const float alpha = a0.w;
     Sym tau;
     bool ok;
     if (MAT == MPM_NEOHOOKEAN) ok = nh_tau(P, Fn, tau);
     else ok = dp_update(P, alpha, Fn, tau);
     sum += tau.xx + tau.yy + tau.zz + tau.xy + tau.xz + tau.yz;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        sum += Fn[k];
-        po[(PF + k) * stride + i] = Fn[k];
-    }
+    for (int k = 0; k < 9; ++k) sum += Fn[k];
     const bool bad = !(ok && isfinite(sum));
-    po[(PT + 0) * stride + i] = tau.xx;
-    po[(PT + 1) * stride + i] = tau.xy;
-    po[(PT + 2) * stride + i] = tau.xz;
-    po[(PT + 3) * stride + i] = tau.yy;
-    po[(PT + 4) * stride + i] = tau.yz;
-    po[(PT + 5) * stride + i] = tau.zz;
-    po[PPHI * stride + i] = alpha;
-    po[PID * stride + i] = ps[PID * stride + p];
+    o4[32] = make_float4(Fn[0], Fn[1], Fn[2], Fn[3]);
+    o4[2 * 32] = make_float4(Fn[4], Fn[5], Fn[6], Fn[7]);
+    o4[3 * 32] = make_float4(Fn[8], a3.y, tau.xx, tau.xy);   // a3.y: the id
+    o4[4 * 32] = make_float4(tau.xz, tau.yy, tau.yz, tau.zz);
     if (bad) raise_flag(st, &st->numeric, 1u);   // after the stores, which it then does not hold back
 }
 
@@ -989,19 +1082,19 @@ __global__ void k_init_stress(float* __restrict__ ps, int64_t stride, int64_t n,
     if (p >= n) return;
     float F[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) F[k] = ps[(PF + k) * stride + p];
+    for (int k = 0; k < 9; ++k) F[k] = ps[pel(p, PF + k)];
     Sym t;
     const bool ok = (P.material == MPM_NEOHOOKEAN) ? nh_tau(P, F, t) : hencky_tau(P, F, t);
     if (!ok) {
         atomicOr(&st->numeric, 1u);
         t = Sym{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     }
-    ps[(PT + 0) * stride + p] = t.xx;
-    ps[(PT + 1) * stride + p] = t.xy;
-    ps[(PT + 2) * stride + p] = t.xz;
-    ps[(PT + 3) * stride + p] = t.yy;
-    ps[(PT + 4) * stride + p] = t.yz;
-    ps[(PT + 5) * stride + p] = t.zz;
+    ps[pel(p, PT + 0)] = t.xx;
+    ps[pel(p, PT + 1)] = t.xy;
+    ps[pel(p, PT + 2)] = t.xz;
+    ps[pel(p, PT + 3)] = t.yy;
+    ps[pel(p, PT + 4)] = t.yz;
+    ps[pel(p, PT + 5)] = t.zz;
 }
 
 // End of a step: count it unless something raised the abort word.
