@@ -3,8 +3,9 @@
 One "step" is one full explicit MPM step through the C-ABI: the active-set
 rebuild (cell keys, hashed insert, compaction, particle sort), P2G, the grid
 update and G2P with the Drucker-Prager return map.  The default workload is
-the 1,048,576-particle granular column collapse (512x512x256 potential grid,
-dx = 1/128).  All inputs are synthetic and seeded.
+the 8,000,000-particle synthetic landslide (2048x1024x256 potential grid,
+dx = 0.5 m, terrain level set), the largest single-GPU configuration of the
+method's benchmarks.  All inputs are synthetic and seeded.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl b300|reference]
 
@@ -373,19 +374,22 @@ def e2e_steps(sim, n, nsteps):
     return float(np.mean(ts)), h2d, h2d
 
 
-def cpu_baseline(wl, nsteps):
-    """The FP64 oracle as it stands, one host core, on `nsteps` full steps of
-    the same workload (its dense grid covers the whole potential box)."""
+def cpu_baseline(wl, nsteps, openmp=False):
+    """The FP64 oracle as it stands on `nsteps` full steps of `wl` (its dense
+    grid covers the whole box of `wl`): one host core, or with `openmp` its
+    all-core build (P2G into per-thread grids, grid update and G2P split over
+    the cores).  Returns (particle-updates/s, seconds, threads used)."""
     import oracle
     o = oracle.Oracle(lo=wl.lo, hi=wl.hi, h=wl.dx, dt=wl.dt, g=wl.gravity, B=wl.block_size, material=wl.material,
                       E=wl.E, nu=wl.nu, rho=wl.rho, phi_deg=wl.phi_deg, ppc=wl.ppc, floor_kind=wl.floor_kind,
                       floor_z=wl.floor_z, floor_mu=wl.floor_mu,
                       terrain=None if wl.terrain is None else wl.terrain.astype(np.float64),
-                      terrain_mu=wl.terrain_mu, wall_layers=wl.wall_layers)
+                      terrain_mu=wl.terrain_mu, wall_layers=wl.wall_layers, openmp=openmp)
     t0 = time.perf_counter()
     o.run(wl.x, wl.v, None, None, wl.phi, nsteps=nsteps)
     dt = time.perf_counter() - t0
-    return wl.n * nsteps / dt, dt
+    threads = int(os.environ.get("OMP_NUM_THREADS", len(os.sched_getaffinity(0)))) if openmp else 1
+    return wl.n * nsteps / dt, dt, threads
 
 
 def adjoint_leg(wl, iters: int, every: int = 20):
@@ -419,6 +423,29 @@ def adjoint_leg(wl, iters: int, every: int = 20):
             "loss": L, "dL_dphi_per_deg": dphi, "dL_dE": dE, "target_phi_deg": 34.0,
             "calibration": {"iters": iters, "phi_deg": [hist[0][0], hist[-1][0]], "loss": [hist[0][1], hist[-1][1]],
                             "seconds": t_cal, "seconds_per_iter": t_cal / max(iters, 1)}}
+
+
+def ensemble_leg(steps: int, stream):
+    """The batched ensemble (64 column collapses of uneven size, each in its
+    own sparse grid, every launch covering all of them) timed like the main
+    line: queued steps between CUDA events, inputs resident on the device."""
+    import torch
+    from paper_2605_28525_b300 import mpm, workloads as W
+    wl = W.column_ensemble()
+    sim = mpm.Simulation.from_workload(wl, flags=0, stream=stream, device_inputs=True)
+    for _ in range(3):
+        sim.step(1)
+    tuning = sim.autotune(3)
+    sim.step(1)
+    torch.cuda.synchronize()
+    ms = float(np.mean(time_steps(sim, steps, None)))
+    st = sim.stats()
+    sim.close()
+    torch.cuda.empty_cache()
+    return {"workload": wl.name, "scenarios": int(len(wl.scenario_counts)), "particles": wl.n, "steps": steps,
+            "ms_per_step": ms, "value": wl.n / (ms * 1e-3), "unit": UNIT, "active_blocks": st["n_active_blocks"],
+            "tuning": {k: tuning[k] for k in ("p2g_ctas_per_sm", "g2p_threads", "g2p_regs")},
+            "step_launch": "one mpm_step call of K steps (one CUDA graph per step, every launch covering all scenarios)"}
 
 
 def occupancy_sweep(boxes=(128, 256, 512, 1024), steps: int = 20):
@@ -523,9 +550,13 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
-    ap.add_argument("--workload", default="column_collapse_1M")
+    ap.add_argument("--workload", default="landslide_8M")
     ap.add_argument("--dense-steps", type=int, default=5)
-    ap.add_argument("--cpu-steps", type=int, default=3)
+    ap.add_argument("--cpu-steps", type=int, default=10,
+                    help="oracle steps of the CPU baseline, over the reference arm's spatial sample")
+    ap.add_argument("--ensemble-steps", type=int, default=100)
+    ap.add_argument("--no-ensemble", action="store_true",
+                    help="skip the batched-ensemble sub-record (column_ensemble_64)")
     ap.add_argument("--no-dense", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -622,6 +653,9 @@ def main():
                  "sparse_speedup": (wl.n / (total_ms / args.steps / 1e3)) / dense_value,
                  "occupancy_nodes": st["n_active_nodes"] / st["n_dense_nodes"]}
 
+    ens = None
+    if not args.no_ensemble and rank == 0 and wl.scenario_counts is None:
+        ens = ensemble_leg(args.ensemble_steps, stream)
     sweep = occupancy_sweep() if (args.sweep and rank == 0) else None
     adj = None
     if args.adjoint and rank == 0:
@@ -631,10 +665,13 @@ def main():
     if rank == 0 and not args.no_cpu:
         from paper_2605_28525_b300 import workloads as W
         cwl = wl if wl.scenario_counts is None else W.ensemble_member(wl, 0)   # the oracle runs one scenario
-        cv, cdt = cpu_baseline(cwl, args.cpu_steps)
+        swl, what = reference_sample(cwl)
+        cv, cdt, _ = cpu_baseline(swl, args.cpu_steps)
+        ov, odt, othr = cpu_baseline(swl, args.cpu_steps, openmp=True)
         cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "%d full FP64 oracle steps of %s (%d particles, dense %s node grid), %.1f s" % (
-                   args.cpu_steps, cwl.name, cwl.n, "x".join(str(cwl.hi[a] - cwl.lo[a] + 1) for a in range(3)), cdt)}
+               "sample": "%d FP64 oracle steps of %s, one core, over %s; %.1f s" % (args.cpu_steps, cwl.name, what, cdt),
+               "all_cores": {"value": ov, "unit": UNIT, "cores": othr, "kind": "oracle (OpenMP build of the same source)",
+                             "sample": "the same %d steps and sample on %d threads; %.1f s" % (args.cpu_steps, othr, odt)}}
 
     if rank == 0:
         line = {
@@ -657,6 +694,7 @@ def main():
             "e2e": e2e,
             "dense_gpu": dense,
             "gpu_launches": launches,
+            **({"ensemble": ens} if ens is not None else {}),
             **({"adjoint": adj} if adj is not None else {}),
             **({"occupancy_sweep": sweep} if sweep is not None else {}),
             "clocks": clk.summary(),

@@ -103,3 +103,17 @@ def test_binding_rejects_bad_inputs_before_creating_a_context():
         mpm.Simulation(cfg, wl.x, phi=np.zeros(wl.n + 1, np.float32))
     with pytest.raises(ValueError):
         mpm.Simulation(cfg, wl.x, terrain=np.zeros(7, np.float32))
+
+
+def test_openmp_oracle_build_matches_serial(oracle_mod):
+    """The all-core build of the oracle (the bench's all-core CPU baseline)
+    computes the serial oracle's trajectory up to FP64 summation order."""
+    import numpy as np
+    from paper_2605_28525_b300 import workloads as W
+    x, v, Cm, F = W.random_state(3000, (10,) * 3, (22,) * 3, 1.0 / 32, seed=9, fscale=0.02)
+    kw = dict(lo=(0, 0, 0), hi=(32, 32, 32), h=1.0 / 32, dt=1e-4, B=4, material=oracle_mod.DRUCKER_PRAGER, E=1e6,
+              phi_deg=30.0, floor_kind=oracle_mod.FLOOR_COULOMB, floor_z=11.0 / 32, floor_mu=0.4)
+    a = oracle_mod.Oracle(**kw).run(x, v, Cm, F, nsteps=3)
+    b = oracle_mod.Oracle(openmp=True, **kw).run(x, v, Cm, F, nsteps=3)
+    for u, w in zip(a, b):
+        assert np.abs(u - w).max() <= 1e-12 * np.abs(u).max()
