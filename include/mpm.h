@@ -225,14 +225,21 @@ mpm_status mpm_get_stats(mpm_ctx* ctx, mpm_stats* out);
  * *n_active (host) their count.  stream: a cudaStream_t or NULL; the call
  * waits for its own work on it.
  * No memory is allocated: the hash table, block list and sort scratch live
- * in one fixed device array of about 2 MiB, held on every GPU that loads the
- * library until the process exits.  Limit: 65,536 active blocks per call;
- * beyond that the call returns MPM_ERR_INVALID_ARG (use mpm_create and
- * mpm_rebuild_active instead).  Other errors: OUT_OF_DOMAIN, NUMERIC, CUDA;
- * the reason is in mpm_last_error(NULL).  Every call clears and reuses the
- * shared array, so calls whose GPU work overlaps (e.g. on two streams) race:
- * serialise them.  The first call on a device looks up the array's address
- * with that device current; make that first call before any stream capture. */
+ * in one fixed device array of about 2 MiB, held on every GPU where it has
+ * been loaded until the process exits.  Limit: 65,536 active blocks per
+ * call, and no more than 128 keys crowding one stretch of its 2^17-slot
+ * table; beyond that the call returns MPM_ERR_INVALID_ARG (use mpm_create
+ * and mpm_rebuild_active instead).  Other errors: OUT_OF_DOMAIN, NUMERIC,
+ * CUDA; the reason is in mpm_last_error(NULL).  Every call clears and
+ * reuses the shared array, so calls whose GPU work overlaps (e.g. on two
+ * streams) race: serialise them.  The first call on a device looks up the
+ * array's address with that device current; make that first call before
+ * any stream capture.  Under CUDA's lazy module loading (the default) that
+ * first call is also what loads the library's device code and the array
+ * onto the device, so it needs free device memory: make it once at
+ * start-up, before a pool takes the GPU; later calls allocate nothing.  The
+ * address is kept for the process's life: do not call this again after a
+ * device reset (cudaDeviceReset). */
 mpm_status mpm_active_blocks_noalloc(const float* x, int64_t n, const int32_t domain_lo[3],
                                      const int32_t domain_hi[3], double dx, int32_t block_size,
                                      uint64_t* block_keys, int64_t cap, int64_t* n_active, void* stream);

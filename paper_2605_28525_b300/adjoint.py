@@ -7,10 +7,12 @@ state kept, then ``mpm_adjoint_step`` is applied step by step from the last
 to the first.  Memory: n / every checkpoints plus ``every`` states.
 
 ``Rollout`` wraps both in a ``torch.autograd.Function``: inputs Young's
-modulus E (a 0-d tensor) and the initial positions and velocities; outputs
-the final positions and velocities, both in particle-id order.  Its backward
-returns dL/dE, dL/dx0 and dL/dv0.  The adjoint covers Neo-Hookean contexts in
-deterministic mode with block size 4 (the library refuses the others).
+modulus E and the friction angle phi (0-d tensors, phi in degrees, one angle
+for every particle) and the initial positions and velocities; outputs the
+final positions and velocities, both in particle-id order.  Its backward
+returns dL/dE, dL/dphi, dL/dx0 and dL/dv0.  The adjoint covers Neo-Hookean
+and Drucker-Prager contexts in deterministic mode with block size 4 (the
+library refuses the others).
 """
 from __future__ import annotations
 

@@ -6,17 +6,26 @@
 // GPU through its own pool, real-time loops that forbid allocation after
 // start-up, or plug-ins that are handed device buffers but no allocator.
 // This entry point serves them.  Its hash table, block list and sort scratch
-// live in one file-scope device array of fixed size, reserved on every GPU
-// that loads the library for as long as the process runs; the caller passes
-// only the particle positions and the output buffer.
+// live in one file-scope device array of fixed size, held on every GPU where
+// it has been loaded for as long as the process runs; the caller passes only
+// the particle positions and the output buffer.
 //
 // Limits: at most NA_MAX_BLOCKS active blocks per call (65,536 blocks, i.e.
-// 4.2 M nodes at block size 4) and a 2^17-slot table; larger sets are
-// rejected with MPM_ERR_INVALID_ARG.  All calls share the one array, so two
-// calls whose GPU work overlaps (for example on two streams) race and
-// produce garbage; serialise them.  The first call on a device looks up the
-// array's device address (cudaGetSymbolAddress) with that device current;
-// make that first call before any stream capture.
+// 4.2 M nodes at block size 4) and a 2^17-slot table probed at most
+// NA_MAX_PROBE slots from a key's home slot; larger sets, and sets whose keys
+// crowd one part of the table, are rejected with MPM_ERR_INVALID_ARG.  All
+// calls share the one array, so two calls whose GPU work overlaps (for
+// example on two streams) race and produce garbage; serialise them.  The
+// first call on a device looks up the array's device address
+// (cudaGetSymbolAddress) with that device current; make that first call
+// before any stream capture.  With CUDA's lazy module loading (the default)
+// that lookup is also what loads the library's device code and places the
+// array in device memory, so the first call on a device does need free
+// device memory (the ~2 MiB array and the code): make it once at start-up,
+// before the caller's pool takes the GPU.  Later calls allocate nothing.
+// The address is kept for the life of the process: after a device reset
+// (cudaDeviceReset) it is stale, so do not call this entry point again in a
+// process that reset the device.
 #include <cmath>
 #include <mutex>
 
@@ -212,10 +221,14 @@ extern "C" mpm_status mpm_active_blocks_noalloc(const float* x, int64_t n, const
     if (e != cudaSuccess) return na_fail(MPM_ERR_CUDA, std::string("insert: ") + cudaGetErrorString(e));
     if (hs.nonfinite) return na_fail(MPM_ERR_NUMERIC, "mpm_active_blocks_noalloc: non-finite particle position");
     if (hs.outside) return na_fail(MPM_ERR_OUT_OF_DOMAIN, "mpm_active_blocks_noalloc: a particle stencil left the box");
-    if (hs.overflow || (int64_t)hs.n_active > NA_MAX_BLOCKS)
+    if ((hs.overflow & 2u) || (int64_t)hs.n_active > NA_MAX_BLOCKS)
         return na_fail(MPM_ERR_INVALID_ARG,
                        "mpm_active_blocks_noalloc: more than 65536 active blocks (the fixed scratch limit); "
                        "use mpm_create / mpm_rebuild_active instead");
+    if (hs.overflow)
+        return na_fail(MPM_ERR_INVALID_ARG,
+                       "mpm_active_blocks_noalloc: a block key found no free slot within 128 probes of its home "
+                       "slot (the fixed 2^17-slot table); use mpm_create / mpm_rebuild_active instead");
     *n_active = (int64_t)hs.n_active;
     if ((int64_t)hs.n_active > cap) return na_fail(MPM_ERR_INVALID_ARG, "mpm_active_blocks_noalloc: cap too small");
     uint32_t* lk = reinterpret_cast<uint32_t*>(scratch + OFF_LKEY);

@@ -1,8 +1,11 @@
 // Stable LSD radix sort of (uint32 key, uint32 value) pairs, 8-bit digits.
 //
-// Used twice per step: to put the active block keys in ascending Eq.-(key)
-// order (the canonical compaction that fixes Phi), and to reorder particles
-// by (block, cell) so that P2G and G2P read and write contiguous runs.
+// The sparse grid needs it only for boxes whose block bit mask would exceed
+// 64 MiB, where it puts the active block keys in ascending Eq.-(key) order
+// (the canonical compaction that fixes Phi; smaller boxes rank blocks by the
+// mask and a popcount, and sort particles by a counting sort).  The dense
+// grid uses it every step to reorder particles by (block, cell, id), and the
+// allocation-free active-set entry point to sort its block keys.
 // Each pass is reduce-then-scan: per-tile digit histograms, a scan of every
 // digit's row of tile counts, and a stable scatter that ranks keys inside a
 // tile with warp match/popc.  The live element count may sit in device
