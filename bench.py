@@ -552,7 +552,7 @@ def main():
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--workload", default="landslide_8M")
     ap.add_argument("--dense-steps", type=int, default=5)
-    ap.add_argument("--cpu-steps", type=int, default=10,
+    ap.add_argument("--cpu-steps", type=int, default=100,
                     help="oracle steps of the CPU baseline, over the reference arm's spatial sample")
     ap.add_argument("--ensemble-steps", type=int, default=100)
     ap.add_argument("--no-ensemble", action="store_true",
