@@ -110,12 +110,6 @@ struct MomAcc {
     float2 m_mz, mxy;
 };
 
-// The planes each pass reads: 0 (x), 5 (v, C0), 6 (C1..C4), 7 (C5..C8) for
-// the momentum; 0 (x), 3 (F8, id, tau xx, xy), 4 (tau xz, yy, yz, zz) for
-// the force.
-__constant__ int kMomPlanes[4] = {0, 5, 6, 7};
-__constant__ int kForcePlanes[4] = {0, 3, 4, 0};
-
 __device__ __forceinline__ void p2g_momentum(const Params& P, const float4 (&pl)[4], MomAcc (&acc)[27]) {
     const float4 a0 = pl[0], a5 = pl[1], a6 = pl[2], a7 = pl[3];
     const float xs[3] = {a0.x, a0.y, a0.z};
@@ -205,8 +199,16 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Rounds each P2G pass stages ahead of the one it sums, plus one: the round
+// being summed waits until at most MPM_P2G_STAGES - 1 later groups are open.
+#ifndef MPM_P2G_STAGES
+#define MPM_P2G_STAGES 2
+#endif
+__device__ __forceinline__ void cp_async_wait_stages() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(MPM_P2G_STAGES - 1) : "memory");
+}
 
 #ifndef MPM_P2G_PCACHE
 #define MPM_P2G_PCACHE 12   // rounds whose particle indices a lane loads once per work unit
@@ -234,7 +236,7 @@ __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, MPM_P2G_MINB) k_p2g_c
 #if MPM_P2G_PCACHE
     __shared__ uint32_t pcs[K::WARPS][MPM_P2G_PCACHE][32];   // the lanes' cached particle indices
 #endif
-    __shared__ __align__(16) float4 stage[K::WARPS][2][4][32];   // the lanes' staged particle planes, 2 rounds
+    __shared__ __align__(16) float4 stage[K::WARPS][MPM_P2G_STAGES][4][32];   // the lanes' staged particle planes
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     float(&tile)[7][K::TILE] = tiles[wid];
     if (cta_aborted(stc)) return;
@@ -309,14 +311,23 @@ __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, MPM_P2G_MINB) k_p2g_c
                 off += nrun;
                 return ok;
             };
-            float4(&sbuf)[2][4][32] = stage[wid];
+            float4(&sbuf)[MPM_P2G_STAGES][4][32] = stage[wid];
             const float4* ps4 = reinterpret_cast<const float4*>(ps);
-            auto stage_planes = [&](bool ok, uint32_t p, int buf, const int* planes, int np) {
+            // the planes each pass reads: 0 (x), 5 (v, C0), 6 (C1..C4), 7 (C5..C8)
+            // for the momentum; 0 (x), 3 (F8, id, tau xx, xy), 4 (tau xz, yy,
+            // yz, zz) for the force
+            auto stage_planes = [&](bool ok, uint32_t p, int buf, bool momentum) {
                 if (ok) {
                     const float4* q4 = ps4 + pel4(p, 0);
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        if (j < np) cp_async16(&sbuf[buf][j][lane], q4 + 32 * planes[j]);
+                    cp_async16(&sbuf[buf][0][lane], q4);
+                    if (momentum) {
+                        cp_async16(&sbuf[buf][1][lane], q4 + 32 * 5);
+                        cp_async16(&sbuf[buf][2][lane], q4 + 32 * 6);
+                        cp_async16(&sbuf[buf][3][lane], q4 + 32 * 7);
+                    } else {
+                        cp_async16(&sbuf[buf][1][lane], q4 + 32 * 3);
+                        cp_async16(&sbuf[buf][2][lane], q4 + 32 * 4);
+                    }
                 }
                 cp_async_commit();
             };
@@ -329,18 +340,25 @@ __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, MPM_P2G_MINB) k_p2g_c
                 for (int q = 0; q < 27; ++q) macc[q].m_mz = macc[q].mxy = make_float2(0.f, 0.f);
                 int off = 0;
                 uint32_t p;
-                bool ok = round_particle(0, off, p);
-                stage_planes(ok && R > 0, p, 0, kMomPlanes, 4);
+                unsigned okm = 0u;   // bit j: round k + j of this lane is staged
+#pragma unroll
+                for (int j = 0; j < MPM_P2G_STAGES - 1; ++j) {
+                    const bool ok = j < R && round_particle(j, off, p);
+                    okm |= (unsigned)ok << j;
+                    stage_planes(ok, p, j, true);
+                }
 #pragma unroll 1
                 for (int k = 0; k < R; ++k) {
-                    const bool cur = ok;
-                    if (k + 1 < R) ok = round_particle(k + 1, off, p);
-                    else ok = false;
-                    stage_planes(ok, p, (k + 1) & 1, kMomPlanes, 4);
-                    cp_async_wait1();
+                    const bool cur = okm & 1u;
+                    const int kn = k + MPM_P2G_STAGES - 1;
+                    const bool ok = kn < R && round_particle(kn, off, p);
+                    okm = (okm >> 1) | ((unsigned)ok << (MPM_P2G_STAGES - 2));
+                    stage_planes(ok, p, kn % MPM_P2G_STAGES, true);
+                    cp_async_wait_stages();
+                    const int kb = k % MPM_P2G_STAGES;
                     if (cur) {
-                        const float4 pl[4] = {sbuf[k & 1][0][lane], sbuf[k & 1][1][lane], sbuf[k & 1][2][lane],
-                                              sbuf[k & 1][3][lane]};
+                        const float4 pl[4] = {sbuf[kb][0][lane], sbuf[kb][1][lane], sbuf[kb][2][lane],
+                                              sbuf[kb][3][lane]};
                         p2g_momentum(P, pl, macc);
                     }
                 }
@@ -366,17 +384,24 @@ __global__ void __launch_bounds__(CellTileCfg::WARPS * 32, MPM_P2G_MINB) k_p2g_c
                 cp_async_wait0();
                 int off = 0;
                 uint32_t p;
-                bool ok = round_particle(0, off, p);
-                stage_planes(ok && R > 0, p, 0, kForcePlanes, 3);
+                unsigned okm = 0u;   // bit j: round k + j of this lane is staged
+#pragma unroll
+                for (int j = 0; j < MPM_P2G_STAGES - 1; ++j) {
+                    const bool ok = j < R && round_particle(j, off, p);
+                    okm |= (unsigned)ok << j;
+                    stage_planes(ok, p, j, false);
+                }
 #pragma unroll 1
                 for (int k = 0; k < R; ++k) {
-                    const bool cur = ok;
-                    if (k + 1 < R) ok = round_particle(k + 1, off, p);
-                    else ok = false;
-                    stage_planes(ok, p, (k + 1) & 1, kForcePlanes, 3);
-                    cp_async_wait1();
+                    const bool cur = okm & 1u;
+                    const int kn = k + MPM_P2G_STAGES - 1;
+                    const bool ok = kn < R && round_particle(kn, off, p);
+                    okm = (okm >> 1) | ((unsigned)ok << (MPM_P2G_STAGES - 2));
+                    stage_planes(ok, p, kn % MPM_P2G_STAGES, false);
+                    cp_async_wait_stages();
+                    const int kb = k % MPM_P2G_STAGES;
                     if (cur) {
-                        const float4 pl[4] = {sbuf[k & 1][0][lane], sbuf[k & 1][1][lane], sbuf[k & 1][2][lane],
+                        const float4 pl[4] = {sbuf[kb][0][lane], sbuf[kb][1][lane], sbuf[kb][2][lane],
                                               make_float4(0.f, 0.f, 0.f, 0.f)};
                         p2g_force(P, pl, facc);
                     }
