@@ -252,10 +252,12 @@ cudaError_t ensure_block_arrays(mpm_ctx* c, int64_t nb) {
     dfree(c, c->nbr, 0);
     dfree(c, c->ccount, 0);
     dfree(c, c->cperm, 0);
+    dfree(c, c->cslot, 0);
+    dfree(c, c->kpre, 0);
     dfree(c, c->hasp, 0);
-    c->bstart = c->bend = c->pblocks = c->nbr = c->ccount = c->hasp = nullptr;
+    c->bstart = c->bend = c->pblocks = c->nbr = c->ccount = c->hasp = c->kpre = nullptr;
     c->bcoord = nullptr;
-    c->cperm = nullptr;
+    c->cperm = c->cslot = nullptr;
     c->brange_cap = 0;
     cudaError_t e;
     if ((e = dalloc(c, (void**)&c->bstart, sizeof(int) * nc)) != cudaSuccess) return e;
@@ -266,6 +268,10 @@ cudaError_t ensure_block_arrays(mpm_ctx* c, int64_t nb) {
         return e;
     if ((e = dalloc(c, (void**)&c->ccount, sizeof(int) * nc * c->B3)) != cudaSuccess) return e;
     if ((e = dalloc(c, (void**)&c->cperm, sizeof(uint8_t) * nc * c->B3)) != cudaSuccess) return e;
+    if (!c->dense && !c->det && c->B == 4) {   // the k-major scatter of the fast sparse mode
+        if ((e = dalloc(c, (void**)&c->cslot, sizeof(uint8_t) * nc * c->B3)) != cudaSuccess) return e;
+        if ((e = dalloc(c, (void**)&c->kpre, sizeof(int) * nc * c->B3)) != cudaSuccess) return e;
+    }
     if ((e = dalloc(c, (void**)&c->hasp, sizeof(int) * nc)) != cudaSuccess) return e;
     // generation 0 never matches a live step: start from a clean table
     if ((e = cudaMemsetAsync(c->hasp, 0, sizeof(int) * nc, c->st)) != cudaSuccess) return e;

@@ -334,6 +334,8 @@ struct mpm_ctx {
     int* pblocks = nullptr;      // Phi of blocks holding particles
     int* ccount = nullptr;       // per (Phi, slot): particles in the slot's cell (k-major P2G order)
     uint8_t* cperm = nullptr;    // per (Phi, slot): the slot's cell (fast mode: cells by count)
+    uint8_t* cslot = nullptr;    // per (Phi, cell): the cell's slot (fast sparse mode)
+    int* kpre = nullptr;         // per (Phi, k < 64): particles of the block's rounds before round k (fast sparse mode)
     int* nbr = nullptr;          // per Phi: Phi of the blocks b + {0..R-1}^3 (R = 2 for B = 4, 3 for B = 1)
     int64_t brange_cap = 0;
     int* bins = nullptr;         // counting sort: particles per (Phi, cell) bin (one per node)

@@ -536,6 +536,43 @@ __device__ __forceinline__ int first_geq(const uint32_t* __restrict__ skey, int 
     return lo;
 }
 
+// Slots of a block's 64 cells ordered by particle count, largest first (ties
+// by cell index): slot of cell c = the cells with more particles, or as many
+// and a smaller index, a permutation of 0..63.  Counts are compared clamped
+// to 63, which only reorders cells fuller than that.  Lane l holds the counts
+// of cells l and l + 32 and gets their slots q0, q1; hall and hlow are 64-int
+// scratch arrays of the calling warp.  Every lane of the warp calls it.
+__device__ __forceinline__ void count_order_slots(int cnt0, int cnt1, int lane, int* hall, int* hlow, int& q0,
+                                                  int& q1) {
+    const unsigned FULL = 0xffffffffu;
+    const int v0 = min(cnt0, 63), v1 = min(cnt1, 63);
+    hall[lane] = hall[lane + 32] = 0;
+    hlow[lane] = hlow[lane + 32] = 0;
+    __syncwarp();
+    atomicAdd(&hall[v0], 1);
+    atomicAdd(&hall[v1], 1);
+    atomicAdd(&hlow[v0], 1);   // cells 0-31 only
+    __syncwarp();
+    // more[v] = cells with a clamped count above v (a suffix sum)
+    const int h0 = hall[lane], h1 = hall[lane + 32];
+    int s1 = h1, s0 = h0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {   // inclusive suffix sums inside each half
+        const int t1 = __shfl_down_sync(FULL, s1, o), t0 = __shfl_down_sync(FULL, s0, o);
+        if (lane + o < 32) {
+            s1 += t1;
+            s0 += t0;
+        }
+    }
+    s0 += __shfl_sync(FULL, s1, 0);   // the upper half lies above every lower value
+    const int more0 = s0 - h0, more1 = s1 - h1;   // for values lane and lane + 32
+    const int m0a = __shfl_sync(FULL, more0, v0 & 31), m0b = __shfl_sync(FULL, more1, v0 & 31);
+    const int m1a = __shfl_sync(FULL, more0, v1 & 31), m1b = __shfl_sync(FULL, more1, v1 & 31);
+    const unsigned below = (1u << lane) - 1u;
+    q0 = (v0 < 32 ? m0a : m0b) + __popc(__match_any_sync(FULL, v0) & below);
+    q1 = (v1 < 32 ? m1a : m1b) + hlow[v1] + __popc(__match_any_sync(FULL, v1) & below);
+}
+
 // Reorders every block's particles from (cell, k) to k-major order: the
 // k-th particle of each cell (cells in slot order) before any (k+1)-th one,
 // and records the particle count per slot.  One warp per block; lane l
@@ -580,38 +617,9 @@ __global__ void __launch_bounds__(128) k_interleave(const uint32_t* __restrict__
         int cnt0 = hi0 - lo0, cnt1 = hi1 - lo1;
         int cell0 = lane, cell1 = lane + 32;
         if (cperm) {
-            // slot of cell c = the cells with more particles, or as many and a
-            // smaller index (a permutation of 0..63); counts are compared
-            // clamped to 63, which only reorders cells fuller than that
             const int w = threadIdx.x >> 5;
-            const int v0 = min(cnt0, 63), v1 = min(cnt1, 63);
-            int* hall = hist_all[w];
-            int* hlow = hist_low[w];
-            hall[lane] = hall[lane + 32] = 0;
-            hlow[lane] = hlow[lane + 32] = 0;
-            __syncwarp();
-            atomicAdd(&hall[v0], 1);
-            atomicAdd(&hall[v1], 1);
-            atomicAdd(&hlow[v0], 1);   // cells 0-31 only
-            __syncwarp();
-            // more[v] = cells with a clamped count above v (a suffix sum)
-            const int h0 = hall[lane], h1 = hall[lane + 32];
-            int s1 = h1, s0 = h0;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {   // inclusive suffix sums inside each half
-                const int t1 = __shfl_down_sync(FULL, s1, o), t0 = __shfl_down_sync(FULL, s0, o);
-                if (lane + o < 32) {
-                    s1 += t1;
-                    s0 += t0;
-                }
-            }
-            s0 += __shfl_sync(FULL, s1, 0);   // the upper half lies above every lower value
-            const int more0 = s0 - h0, more1 = s1 - h1;   // for values lane and lane + 32
-            const int m0a = __shfl_sync(FULL, more0, v0 & 31), m0b = __shfl_sync(FULL, more1, v0 & 31);
-            const int m1a = __shfl_sync(FULL, more0, v1 & 31), m1b = __shfl_sync(FULL, more1, v1 & 31);
-            const unsigned below = (1u << lane) - 1u;
-            const int q0 = (v0 < 32 ? m0a : m0b) + __popc(__match_any_sync(FULL, v0) & below);
-            const int q1 = (v1 < 32 ? m1a : m1b) + hlow[v1] + __popc(__match_any_sync(FULL, v1) & below);
+            int q0, q1;
+            count_order_slots(cnt0, cnt1, lane, hist_all[w], hist_low[w], q0, q1);
             unsigned char* sc = slot_cell[w];
             sc[q0] = (unsigned char)lane;
             sc[q1] = (unsigned char)(lane + 32);
@@ -970,6 +978,118 @@ __global__ void k_block_ranges(int64_t cap, int B3, const int* __restrict__ cs, 
     }
 }
 
+// ------------------------------- k-major scatter (fast sparse mode, B = 4)
+//
+// With a block's slots ordered by count, largest first, the cells that still
+// hold a particle in round k are exactly slots 0 .. n_k - 1 (n_k = cells with
+// more than k particles).  So the k-major position of the particle of rank k
+// in the cell of slot s is fixed by the counts alone:
+//     block start + sum_c min(count_c, k) + s,
+// and the counting sort can scatter particles straight to it, with no
+// cell-major pass in between.
+
+// One warp per active block (grid-stride): the block's particle range and
+// the "holds particles" mark, its neighbour table, the count order of its
+// cells (cperm: slot -> cell, cslot: cell -> slot, ccount per slot) and the
+// round prefixes kpre[k] = sum_c min(count_c, k) for k < 64.
+__global__ void __launch_bounds__(128) k_block_prep(int64_t cap, const int* __restrict__ cs,
+                                                    const int* __restrict__ tsum, int ntiles, int* __restrict__ bstart,
+                                                    int* __restrict__ bend, int* __restrict__ pblocks,
+                                                    int* __restrict__ hasp, DevStatus* st,
+                                                    const int4* __restrict__ bcoord, Params P, HashView hv,
+                                                    int* __restrict__ nbr, int* __restrict__ ccount,
+                                                    uint8_t* __restrict__ cperm, uint8_t* __restrict__ cslot,
+                                                    int* __restrict__ kpre) {
+    __shared__ int hist_all[4][64], hist_low[4][64];
+    if (cta_aborted(st)) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int gw = blockIdx.x * 4 + w, nw = gridDim.x * 4;
+    const unsigned FULL = 0xffffffffu;
+    const int64_t nact = live_blocks(st, cap);
+    const int64_t n = nact * 64;
+    const int gen = (int)st->gen;
+    for (int64_t r = gw; r < nact; r += nw) {
+        if (lane < 8) {
+            const int4 b = bcoord[r];
+            nbr[r * 8 + lane] = lookup_block(P, hv, b.x + (lane >> 2), b.y + ((lane >> 1) & 1), b.z + (lane & 1));
+        }
+        const int64_t base = r * 64;
+        const int lo0 = scan_at(cs, tsum, base + lane, n, ntiles), hi0 = scan_at(cs, tsum, base + lane + 1, n, ntiles);
+        const int lo1 = scan_at(cs, tsum, base + 32 + lane, n, ntiles);
+        const int hi1 = scan_at(cs, tsum, base + 33 + lane, n, ntiles);
+        const int cnt0 = hi0 - lo0, cnt1 = hi1 - lo1;
+        const int s = __shfl_sync(FULL, lo0, 0), e = __shfl_sync(FULL, hi1, 31);
+        if (e <= s) continue;   // warp-uniform: no particle in this block
+        if (lane == 0) {
+            bstart[r] = s;
+            bend[r] = e;
+            hasp[r] = gen;
+            pblocks[atomicAdd(&st->n_pblocks, 1u)] = (int)r;
+        }
+        int q0, q1;
+        count_order_slots(cnt0, cnt1, lane, hist_all[w], hist_low[w], q0, q1);
+        cslot[base + lane] = (uint8_t)q0;
+        cslot[base + 32 + lane] = (uint8_t)q1;
+        cperm[base + q0] = (uint8_t)lane;
+        cperm[base + q1] = (uint8_t)(lane + 32);
+        ccount[base + q0] = cnt0;
+        ccount[base + q1] = cnt1;
+        // kpre[k] for k = lane and lane + 32
+        int pa = 0, pb = 0;
+#pragma unroll 8
+        for (int j = 0; j < 32; ++j) {
+            const int c0 = __shfl_sync(FULL, cnt0, j), c1 = __shfl_sync(FULL, cnt1, j);
+            pa += min(c0, lane) + min(c1, lane);
+            pb += min(c0, lane + 32) + min(c1, lane + 32);
+        }
+        kpre[base + lane] = pa;
+        kpre[base + 32 + lane] = pb;
+    }
+}
+
+// Per particle (two per lane): its k-major position from its (block, cell)
+// key and its rank in the cell, then the sort key and permutation there.  A
+// rank of 64 or more (a cell that full) sums the block's 64 slot counts.
+__global__ void __launch_bounds__(256) k_scatter_kmajor(int64_t n, const uint32_t* __restrict__ key,
+                                                        const uint32_t* __restrict__ prank,
+                                                        const int* __restrict__ bstart,
+                                                        const uint8_t* __restrict__ cslot,
+                                                        const int* __restrict__ kpre, const int* __restrict__ ccount,
+                                                        uint32_t* __restrict__ skey, uint32_t* __restrict__ perm,
+                                                        DevStatus* st) {
+    if (cta_aborted(st)) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * SCT_PL + lane;
+    uint32_t k[SCT_PL], rk[SCT_PL];
+#pragma unroll
+    for (int h = 0; h < SCT_PL; ++h) {
+        const int64_t p = p0 + 32 * h;
+        k[h] = 0xffffffffu;
+        rk[h] = 0u;
+        if (p < n) {
+            k[h] = key[p];
+            rk[h] = prank[p];
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < SCT_PL; ++h) {
+        if (k[h] == 0xffffffffu) continue;
+        const int64_t r = k[h] >> 6;
+        int pre;
+        if (rk[h] < 64u) {
+            pre = kpre[r * 64 + rk[h]];
+        } else {
+            pre = 0;
+            for (int j = 0; j < 64; ++j) pre += min(ccount[r * 64 + j], (int)rk[h]);
+        }
+        const int pos = bstart[r] + pre + (int)cslot[k[h]];
+        if (!index_ok(pos, n, st)) continue;
+        skey[pos] = k[h];
+        perm[pos] = (uint32_t)(p0 + 32 * h);
+    }
+}
+
+
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 }  // namespace
 
@@ -1072,6 +1192,12 @@ cudaError_t launch_assign(mpm_ctx* c) {
 // is (block, cell, id) as the dense grid's radix sort by (key, id) gives.
 bool counting_sort(const mpm_ctx* c) { return !c->dense; }
 
+// The fast sparse mode at B = 4 scatters particles straight to their k-major
+// positions (k_block_prep, k_scatter_kmajor); the deterministic mode keeps
+// the cell-major scatter and the interleave, which puts each cell's
+// particles in id order.
+static bool kmajor_scatter(const mpm_ctx* c) { return counting_sort(c) && !c->det && c->B == 4; }
+
 cudaError_t launch_particle_keys(mpm_ctx* c) {
     const float* ps = c->ps[c->cur];
     const int64_t cap = c->live_cap;
@@ -1082,9 +1208,11 @@ cudaError_t launch_particle_keys(mpm_ctx* c) {
                                                                   c->prank, c->dstat);
         const int ntiles = (int)((nkeys + SC_TILE - 1) / SC_TILE);
         k_scan_tiles<<<ntiles, SC_THREADS, 0, c->ls>>>(c->bins, cap, c->B3, c->dstat, c->cs, c->tsum);
+        c->launches += 2;
+        if (kmajor_scatter(c)) return cudaGetLastError();   // launch_ranges scatters
         k_bin_scatter<<<blocks_for(c->n, 256 * SCT_PL), 256, 0, c->ls>>>(c->n, c->pkey[0], c->prank, c->cs, c->tsum,
                                                                          c->pkey[1], c->pval[1], c->dstat);
-        c->launches += 3;
+        ++c->launches;
         c->sorted_sel = 1;
         return cudaGetLastError();
     }
@@ -1107,6 +1235,17 @@ cudaError_t launch_ranges(mpm_ctx* c, const uint32_t* skey) {
     const bool cnt = counting_sort(c);
     const int64_t cap = c->live_cap;
     const int ntiles = (int)((cap * c->B3 + SC_TILE - 1) / SC_TILE);   // the bin scan's tiles
+    if (kmajor_scatter(c)) {
+        k_block_prep<<<148 * 8, 128, 0, c->ls>>>(cap, c->cs, c->tsum, ntiles, c->bstart, c->bend, c->pblocks, c->hasp,
+                                                 c->dstat, c->bcoord, c->P, hash_view(c), c->nbr, c->ccount, c->cperm,
+                                                 c->cslot, c->kpre);
+        k_scatter_kmajor<<<blocks_for(c->n, 256 * SCT_PL), 256, 0, c->ls>>>(c->n, c->pkey[0], c->prank, c->bstart,
+                                                                            c->cslot, c->kpre, c->ccount, c->pkey[1],
+                                                                            c->pval[1], c->dstat);
+        c->launches += 2;
+        c->sorted_sel = 1;
+        return cudaGetLastError();
+    }
     if (cnt) {
         const HashView hv = hash_view(c);
         if (c->B == 4)
