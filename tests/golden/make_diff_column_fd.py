@@ -10,7 +10,8 @@ position after 400 steps against a target run at phi = 34 deg:
     R(x) = (mean_p r_p^8)^(1/8),  r_p = horizontal distance of particle p
            from the column's initial axis (mean initial x, y),
 
-the smooth runout measure of the differentiable column.  Every trajectory,
+the smooth runout measure of the differentiable column.  The runout and mean
+position of every trajectory are stored as well.  Every trajectory,
 the target's included, is the serial FP64 oracle's; nothing here comes from
 the CUDA library.  The derivatives are central differences at three step
 sizes each, so that their agreement (the step-size study) shows whether the
@@ -95,6 +96,10 @@ def main():
         "loss": L((PHI0, E0)),
         "dL_dphi_per_deg": {"%g" % h: (L((PHI0 + h, E0)) - L((PHI0 - h, E0))) / (2 * h) for h in PHI_STEPS},
         "dL_dE": {"%g" % h: (L((PHI0, E0 * (1 + h))) - L((PHI0, E0 * (1 - h)))) / (2 * h * E0) for h in E_STEPS},
+        # the runout and mean position of every trajectory, so that the
+        # derivatives of other functionals of them can be formed too
+        "runs": [{"phi_deg": k[0], "E": k[1], "runout": runout(x, axis), "mean": [float(v) for v in x.mean(0)]}
+                 for k, (x, _) in sorted(res.items())],
         "oracle_seconds_per_run": float(np.mean([t for _, t in res.values()])),
         "wall_seconds": time.perf_counter() - t0,
     }

@@ -231,3 +231,67 @@ def test_column_functional_gradient_matches_fp64(oracle_mod):
     assert fdp != 0.0 and fdE != 0.0
     assert abs(float(pt.grad) - fdp) <= 1e-3 * abs(fdp), (float(pt.grad), fdp)
     assert abs(float(Et.grad) - fdE) <= 1e-3 * abs(fdE), (float(Et.grad), fdE)
+
+
+def _golden_diff_column():
+    import json
+    import os
+    return json.load(open(os.path.join(os.path.dirname(__file__), "golden", "diff_column_fd.json")))
+
+
+def test_diff_column_gradients_at_full_configuration(oracle_mod):
+    """The differentiable column exactly as configured: 262,144 particles,
+    Drucker-Prager phi = 30 deg, E = 5e6 Pa, 400 steps with gravity on the
+    Coulomb floor, checkpoints every 20 steps.  The loss (squared error of
+    the runout and mean position against the phi = 34 deg run) and its
+    gradient through the checkpointed adjoint, against FP64 central
+    differences of the oracle's trajectories (tests/golden/diff_column_fd.json,
+    written by make_diff_column_fd.py beside it; the target run is the
+    oracle's too).  The stored step-size study (three step sizes per
+    parameter agreeing to 2e-5) shows the loss is smooth at this point.
+    Also the gradient of the runout plus a weighted mean position, a
+    functional of the trajectory alone (no target residual)."""
+    import torch
+    from paper_2605_28525_b300 import adjoint
+    g = _golden_diff_column()
+    wl = W.diff_column()
+    cfg = g["config"]
+    assert (wl.n, wl.steps, wl.phi_deg, wl.E) == (cfg["particles"], cfg["steps"], cfg["phi_deg"], cfg["E"])
+    assert tuple(cfg["axis"]) == adjoint._axis(wl)
+    fdp = g["dL_dphi_per_deg"]["0.001"]
+    fdE = g["dL_dE"]["0.0001"]
+    # the step-size study: the central differences agree across step sizes
+    assert max(abs(v - fdp) for v in g["dL_dphi_per_deg"].values()) <= 1e-4 * abs(fdp)
+    assert max(abs(v - fdE) for v in g["dL_dE"].values()) <= 1e-4 * abs(fdE)
+    target = (g["target"]["runout"], torch.tensor(g["target"]["mean"], dtype=torch.float64, device="cuda"))
+    L, dphi, dE = adjoint.column_value_and_grad(wl, wl.phi_deg, wl.E, target, wl.steps, 20)
+    assert abs(L - g["loss"]) <= 1e-2 * g["loss"], (L, g["loss"])
+    assert abs(dphi - fdp) <= 1e-3 * abs(fdp), (dphi, fdp)
+    assert abs(dE - fdE) <= 1e-3 * abs(fdE), (dE, fdE)
+
+    # J = R + w . mean(x): the trajectory's own functional, from the stored runs
+    w = np.array([0.3, 0.2, 1.0])
+
+    def J_run(phi, E):
+        r = [r for r in g["runs"] if abs(r["phi_deg"] - phi) < 1e-9 and abs(r["E"] - E) < 1e-6 * E]
+        assert len(r) == 1, (phi, E)
+        return r[0]["runout"] + float(np.dot(w, r[0]["mean"]))
+
+    hp, he = 1e-3, 1e-4
+    fJp = (J_run(wl.phi_deg + hp, wl.E) - J_run(wl.phi_deg - hp, wl.E)) / (2 * hp)
+    fJE = (J_run(wl.phi_deg, wl.E * (1 + he)) - J_run(wl.phi_deg, wl.E * (1 - he))) / (2 * he * wl.E)
+    axis = adjoint._axis(wl)
+    wt = torch.tensor(w, dtype=torch.float64, device="cuda")
+
+    def make_sim(E_, phi_, x0_, v0_):
+        import dataclasses
+        return mpm.Simulation(mpm.config_from_workload(dataclasses.replace(wl, E=E_, phi_deg=phi_),
+                                                       flags=mpm.DETERMINISTIC), x0_, v0_)
+
+    Et = torch.tensor(wl.E, dtype=torch.float64, requires_grad=True)
+    pt = torch.tensor(wl.phi_deg, dtype=torch.float64, requires_grad=True)
+    x0 = torch.tensor(wl.x, device="cuda")
+    xK, _ = adjoint.Rollout.apply(Et, pt, x0, torch.zeros_like(x0), make_sim, wl.steps, 20)
+    (adjoint.runout(xK, axis) + (xK.double().mean(0) * wt).sum()).backward()
+    assert abs(float(pt.grad) - fJp) <= 1e-3 * abs(fJp), (float(pt.grad), fJp)
+    assert abs(float(Et.grad) - fJE) <= 1e-3 * abs(fJE), (float(Et.grad), fJE)
