@@ -540,10 +540,12 @@ __device__ __forceinline__ int first_geq(const uint32_t* __restrict__ skey, int 
 // by cell index): slot of cell c = the cells with more particles, or as many
 // and a smaller index, a permutation of 0..63.  Counts are compared clamped
 // to 63, which only reorders cells fuller than that.  Lane l holds the counts
-// of cells l and l + 32 and gets their slots q0, q1; hall and hlow are 64-int
-// scratch arrays of the calling warp.  Every lane of the warp calls it.
+// of cells l and l + 32 and gets their slots q0, q1, and in more0, more1 the
+// number of cells holding more than l and l + 32 particles (exact below 63);
+// hall and hlow are 64-int scratch arrays of the calling warp.  Every lane of
+// the warp calls it.
 __device__ __forceinline__ void count_order_slots(int cnt0, int cnt1, int lane, int* hall, int* hlow, int& q0,
-                                                  int& q1) {
+                                                  int& q1, int& more0, int& more1) {
     const unsigned FULL = 0xffffffffu;
     const int v0 = min(cnt0, 63), v1 = min(cnt1, 63);
     hall[lane] = hall[lane + 32] = 0;
@@ -565,7 +567,8 @@ __device__ __forceinline__ void count_order_slots(int cnt0, int cnt1, int lane, 
         }
     }
     s0 += __shfl_sync(FULL, s1, 0);   // the upper half lies above every lower value
-    const int more0 = s0 - h0, more1 = s1 - h1;   // for values lane and lane + 32
+    more0 = s0 - h0;   // for values lane and lane + 32
+    more1 = s1 - h1;
     const int m0a = __shfl_sync(FULL, more0, v0 & 31), m0b = __shfl_sync(FULL, more1, v0 & 31);
     const int m1a = __shfl_sync(FULL, more0, v1 & 31), m1b = __shfl_sync(FULL, more1, v1 & 31);
     const unsigned below = (1u << lane) - 1u;
@@ -618,8 +621,8 @@ __global__ void __launch_bounds__(128) k_interleave(const uint32_t* __restrict__
         int cell0 = lane, cell1 = lane + 32;
         if (cperm) {
             const int w = threadIdx.x >> 5;
-            int q0, q1;
-            count_order_slots(cnt0, cnt1, lane, hist_all[w], hist_low[w], q0, q1);
+            int q0, q1, more0, more1;
+            count_order_slots(cnt0, cnt1, lane, hist_all[w], hist_low[w], q0, q1, more0, more1);
             unsigned char* sc = slot_cell[w];
             sc[q0] = (unsigned char)lane;
             sc[q1] = (unsigned char)(lane + 32);
@@ -988,7 +991,8 @@ __global__ void k_block_ranges(int64_t cap, int B3, const int* __restrict__ cs, 
 // and the counting sort can scatter particles straight to it, with no
 // cell-major pass in between.
 
-// One warp per active block (grid-stride): the block's particle range and
+// One warp per active block (one warp per block of the capacity, grid-stride
+// beyond it): the block's particle range and
 // the "holds particles" mark, its neighbour table, the count order of its
 // cells (cperm: slot -> cell, cslot: cell -> slot, ccount per slot) and the
 // round prefixes kpre[k] = sum_c min(count_c, k) for k < 64.
@@ -1026,24 +1030,29 @@ __global__ void __launch_bounds__(128) k_block_prep(int64_t cap, const int* __re
             hasp[r] = gen;
             pblocks[atomicAdd(&st->n_pblocks, 1u)] = (int)r;
         }
-        int q0, q1;
-        count_order_slots(cnt0, cnt1, lane, hist_all[w], hist_low[w], q0, q1);
+        int q0, q1, n0, n1;
+        count_order_slots(cnt0, cnt1, lane, hist_all[w], hist_low[w], q0, q1, n0, n1);
         cslot[base + lane] = (uint8_t)q0;
         cslot[base + 32 + lane] = (uint8_t)q1;
         cperm[base + q0] = (uint8_t)lane;
         cperm[base + q1] = (uint8_t)(lane + 32);
         ccount[base + q0] = cnt0;
         ccount[base + q1] = cnt1;
-        // kpre[k] for k = lane and lane + 32
-        int pa = 0, pb = 0;
-#pragma unroll 8
-        for (int j = 0; j < 32; ++j) {
-            const int c0 = __shfl_sync(FULL, cnt0, j), c1 = __shfl_sync(FULL, cnt1, j);
-            pa += min(c0, lane) + min(c1, lane);
-            pb += min(c0, lane + 32) + min(c1, lane + 32);
+        // kpre[k] = sum_c min(count_c, k) = sum over k' < k of the cells
+        // holding more than k' particles (n0, n1 for k' = lane, lane + 32):
+        // an exclusive scan over k = 0..63
+        int i0 = n0, i1 = n1;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {   // inclusive scans inside each half
+            const int t0 = __shfl_up_sync(FULL, i0, o), t1 = __shfl_up_sync(FULL, i1, o);
+            if (lane >= o) {
+                i0 += t0;
+                i1 += t1;
+            }
         }
-        kpre[base + lane] = pa;
-        kpre[base + 32 + lane] = pb;
+        i1 += __shfl_sync(FULL, i0, 31);
+        kpre[base + lane] = i0 - n0;
+        kpre[base + 32 + lane] = i1 - n1;
     }
 }
 
@@ -1236,7 +1245,7 @@ cudaError_t launch_ranges(mpm_ctx* c, const uint32_t* skey) {
     const int64_t cap = c->live_cap;
     const int ntiles = (int)((cap * c->B3 + SC_TILE - 1) / SC_TILE);   // the bin scan's tiles
     if (kmajor_scatter(c)) {
-        k_block_prep<<<148 * 8, 128, 0, c->ls>>>(cap, c->cs, c->tsum, ntiles, c->bstart, c->bend, c->pblocks, c->hasp,
+        k_block_prep<<<blocks_for(cap, 4), 128, 0, c->ls>>>(cap, c->cs, c->tsum, ntiles, c->bstart, c->bend, c->pblocks, c->hasp,
                                                  c->dstat, c->bcoord, c->P, hash_view(c), c->nbr, c->ccount, c->cperm,
                                                  c->cslot, c->kpre);
         k_scatter_kmajor<<<blocks_for(c->n, 256 * SCT_PL), 256, 0, c->ls>>>(c->n, c->pkey[0], c->prank, c->bstart,
