@@ -250,7 +250,7 @@ mpm_status mpm_active_blocks_noalloc(const float* x, int64_t n, const int32_t do
 typedef struct mpm_tuning {
     int32_t p2g_ctas_per_sm;   /* 1..8 (default: the most that fit on an SM) */
     int32_t g2p_threads;       /* 128 (default) or 256 */
-    int32_t g2p_regs;          /* registers a G2P thread is compiled for: 72 (default; 128 threads only), 80 or 128 */
+    int32_t g2p_regs;          /* registers a G2P thread is compiled for: 72 (default) or 96 (128 threads only), 80 or 128 */
     int32_t reserved;
     double p2g_ms, g2p_ms;     /* mpm_autotune: median device time of the chosen shapes */
 } mpm_tuning;
@@ -258,7 +258,7 @@ typedef struct mpm_tuning {
 /* Autotuner: runs one rebuild on the current state, then times P2G for each
  * p2g_ctas_per_sm from 1 to the most that fit on an SM, and G2P for each
  * (g2p_threads, g2p_regs) in
- * {(128, 72), (128, 80), (128, 128), (256, 80), (256, 128)}, `repeats` times each (CUDA events on the context's
+ * {(128, 72), (128, 80), (128, 96), (128, 128), (256, 80), (256, 128)}, `repeats` times each (CUDA events on the context's
  * stream; the grid is cleared before every P2G), and keeps the shapes with
  * the smallest median.  The particle state is not advanced: the step it
  * timed is discarded.  Synchronises.  *out (nullable) receives the choice.

@@ -1072,7 +1072,7 @@ mpm_status mpm_autotune(mpm_ctx* c, int32_t repeats, mpm_tuning* out) {
     CK(launch_p2g(c));
     CK(launch_grid_update(c));
     // G2P reads the current buffer and writes the other one: reruns repeat it
-    static const int shapes[][2] = {{128, 72}, {128, 80}, {128, 128}, {256, 80}, {256, 128}};
+    static const int shapes[][2] = {{128, 72}, {128, 80}, {128, 96}, {128, 128}, {256, 80}, {256, 128}};
     for (const auto& sh : shapes) {
         c->tune.g2p_threads = sh[0];
         c->tune.g2p_regs = sh[1];
@@ -1108,10 +1108,10 @@ mpm_status mpm_get_tuning(mpm_ctx* c, mpm_tuning* out) {
 mpm_status mpm_set_tuning(mpm_ctx* c, const mpm_tuning* in) {
     if (!c || !in) return MPM_ERR_INVALID_ARG;
     if (in->p2g_ctas_per_sm < 1 || in->p2g_ctas_per_sm > 8 || (in->g2p_threads != 128 && in->g2p_threads != 256) ||
-        (in->g2p_regs != 72 && in->g2p_regs != 80 && in->g2p_regs != 128) ||
-        (in->g2p_regs == 72 && in->g2p_threads != 128))
+        (in->g2p_regs != 72 && in->g2p_regs != 80 && in->g2p_regs != 96 && in->g2p_regs != 128) ||
+        ((in->g2p_regs == 72 || in->g2p_regs == 96) && in->g2p_threads != 128))
         return fail(c, MPM_ERR_INVALID_ARG, "tuning outside p2g_ctas_per_sm 1..8, g2p_threads 128/256, "
-                                            "g2p_regs 72 (128 threads only), 80, 128");
+                                            "g2p_regs 72 or 96 (128 threads only), 80, 128");
     c->tune.p2g_ctas_per_sm = in->p2g_ctas_per_sm;
     c->tune.g2p_threads = in->g2p_threads;
     c->tune.g2p_regs = in->g2p_regs;

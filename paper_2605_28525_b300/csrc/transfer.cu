@@ -1197,6 +1197,7 @@ cudaError_t launch_g2p(mpm_ctx* c) {
             else MPM_G2P_TR(B_, D_, M_, 256, 80);                                                                \
         } else {                                                                                                 \
             if (regs == 128) MPM_G2P_TR(B_, D_, M_, 128, 128);                                                   \
+            else if (regs == 96) MPM_G2P_TR(B_, D_, M_, 128, 96);                                                \
             else if (regs == 80) MPM_G2P_TR(B_, D_, M_, 128, 80);                                                \
             else MPM_G2P_TR(B_, D_, M_, 128, 72);                                                                \
         }                                                                                                        \
