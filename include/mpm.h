@@ -260,7 +260,8 @@ typedef struct mpm_tuning {
  * (g2p_threads, g2p_regs) in
  * {(128, 72), (128, 80), (128, 96), (128, 128), (256, 80), (256, 128)}, `repeats` times each (CUDA events on the context's
  * stream; the grid is cleared before every P2G), and keeps the shapes with
- * the smallest median.  The particle state is not advanced: the step it
+ * the smallest median; the default shapes are timed first and are replaced
+ * only by a shape at least 3% faster.  The particle state is not advanced: the step it
  * timed is discarded.  Synchronises.  *out (nullable) receives the choice.
  * Errors: those of mpm_rebuild_active; INVALID_ARG for repeats < 1. */
 mpm_status mpm_autotune(mpm_ctx* ctx, int32_t repeats, mpm_tuning* out);
