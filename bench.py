@@ -634,6 +634,13 @@ def main():
     achieved = alg_bytes / (phases[dom] * 1e-3) / 1e9
     # the counters were taken in the fast mode; the deterministic P2G is another kernel
     traffic = None if args.deterministic else measured_traffic(wl.name, dom)
+    # both transfer kernels against their own byte models, the dominant one included
+    per_kernel = {}
+    for k in ("p2g", "g2p"):
+        kb = wl.n * ALG_BYTES[k][0] + st["n_active_nodes"] * ALG_BYTES[k][1]
+        ka = kb / (phases[k] * 1e-3) / 1e9
+        per_kernel[k] = {"achieved": ka, "frac": ka / peak, "alg_bytes_per_launch": kb, "kernel_ms": phases[k],
+                         "traffic": None if args.deterministic else measured_traffic(wl.name, k)}
 
     e2e = None
     if not args.no_e2e:
@@ -687,7 +694,7 @@ def main():
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-                         "alg_bytes_per_launch": alg_bytes, "kernel_ms": phases[dom]},
+                         "alg_bytes_per_launch": alg_bytes, "kernel_ms": phases[dom], "kernels": per_kernel},
             "phases_ms": phases,
             "alu_check": None if args.deterministic else alu_check(wl, phases, (clk.summary() or {}).get("sm_mhz")),
             "cpu_baseline": cpu,
