@@ -271,8 +271,15 @@ constexpr int INS_PL = MPM_INSERT_PER_LANE;   // particles per lane in the inser
 // particles when they share their base block, else lanes 0-7 take the first
 // half's offsets and lanes 16-23 the second's.  Otherwise each half is
 // inserted as one group after the other.
+// Registers capped for MPM_INSERT_MINB CTAs per SM (8: 64 warps): the
+// insert waits on its coordinate loads and probes, and more warps in flight
+// hide more of that (the 8M landslide's step 2% faster than at 39 registers
+// and 6 CTAs).
+#ifndef MPM_INSERT_MINB
+#define MPM_INSERT_MINB 8
+#endif
 template <int B, bool SCAN>
-__global__ void __launch_bounds__(256) k_insert(const float* __restrict__ ps, int64_t stride, int64_t n,
+__global__ void __launch_bounds__(256, MPM_INSERT_MINB) k_insert(const float* __restrict__ ps, int64_t stride, int64_t n,
                                                 Params P, HashView hv, uint32_t* __restrict__ akey,
                                                 uint32_t* __restrict__ aslot, int64_t cap,
                                                 uint32_t* __restrict__ bmask, uint32_t* __restrict__ pcode,
