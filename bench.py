@@ -374,6 +374,34 @@ def e2e_steps(sim, n, nsteps):
     return float(np.mean(ts)), h2d, h2d
 
 
+def link_copies(nbytes, reps=3):
+    """Plain pinned host <-> device copies of `nbytes` each way (one
+    cudaMemcpyAsync per direction, CUDA events on the copying stream): the
+    host link's own rate, against which the end-to-end step is read.
+    Returns (host->device GB/s, device->host GB/s, ms for both)."""
+    import torch
+    n = max(1, nbytes // 4)
+    h = torch.empty(n, dtype=torch.float32, pin_memory=True)
+    d = torch.empty(n, dtype=torch.float32, device="cuda")
+    d.copy_(h, non_blocking=True)
+    h.copy_(d, non_blocking=True)
+    torch.cuda.synchronize()
+    up, down = [], []
+    for _ in range(reps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record()
+        d.copy_(h, non_blocking=True)
+        ev[1].record()
+        h.copy_(d, non_blocking=True)
+        ev[2].record()
+        ev[2].synchronize()
+        up.append(ev[0].elapsed_time(ev[1]))
+        down.append(ev[1].elapsed_time(ev[2]))
+    tu, td = float(np.median(up)), float(np.median(down))
+    del h, d
+    return 4 * n / tu / 1e6, 4 * n / td / 1e6, tu + td
+
+
 def cpu_baseline(wl, nsteps, openmp=False):
     """The FP64 oracle as it stands on `nsteps` full steps of `wl` (its dense
     grid covers the whole box of `wl`): one host core, or with `openmp` its
@@ -646,6 +674,10 @@ def main():
     if not args.no_e2e:
         t_e2e, h2d, d2h = e2e_steps(sim, wl.n, max(3, min(args.steps, 5)))
         e2e = {"value": wl.n * ws / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        up, down, copy_ms = link_copies(h2d)
+        # the same bytes as plain pinned copies: what the host link alone takes
+        e2e["link"] = {"h2d_gbs": up, "d2h_gbs": down, "copies_ms_per_step": copy_ms,
+                       "e2e_ms_per_step": 1e3 * t_e2e}
     sim.close()
 
     dense = None
