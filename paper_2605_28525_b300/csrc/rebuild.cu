@@ -284,20 +284,21 @@ __global__ void __launch_bounds__(256, MPM_INSERT_MINB) k_insert(const float* __
                                                 uint32_t* __restrict__ aslot, int64_t cap,
                                                 uint32_t* __restrict__ bmask, uint32_t* __restrict__ pcode,
                                                 DevStatus* st) {
-    if (st->go == 0u) return;   // written by the clear before this kernel: uniform
     const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
     const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * INS_PL + lane;
     float xs[INS_PL][3];
 #pragma unroll
     for (int h = 0; h < INS_PL; ++h) {
-        // plane 0 of the particle: x and alpha
+        // plane 0 of the particle: x and alpha (read before the go test: in
+        // bounds, and its latency overlaps the test's)
         const float4 a0 = (p0 + 32 * h < n) ? reinterpret_cast<const float4*>(ps)[pel4(p0 + 32 * h, 0)]
                                              : make_float4(0.f, 0.f, 0.f, 0.f);
         xs[h][0] = a0.x;
         xs[h][1] = a0.y;
         xs[h][2] = a0.z;
     }
+    if (st->go == 0u) return;   // written by the clear before this kernel: uniform
     unsigned err = 0u;
     Stencil<B> t[INS_PL];
 #pragma unroll
@@ -698,10 +699,9 @@ __global__ void __launch_bounds__(128) k_interleave(const uint32_t* __restrict__
 // atomic add by their leader.  Each warp takes 32 x BIN_PL consecutive
 // particles, BIN_PL per lane, so that as many chains of dependent loads are in
 // flight per lane.
-__device__ __forceinline__ uint32_t bin_key(int64_t p, int64_t n, const uint32_t* __restrict__ pcode,
-                                            const HashView& hv, int B3, DevStatus* st, bool& miss) {
+__device__ __forceinline__ uint32_t bin_key(int64_t p, int64_t n, uint32_t code, const HashView& hv, int B3,
+                                            DevStatus* st, bool& miss) {
     if (p >= n) return 0xffffffffu;
-    const uint32_t code = pcode[p];
     const uint32_t q = code / (uint32_t)B3;
     if (code != 0xffffffffu && !hv.bits && !index_ok(q, (int64_t)hv.mask + 1, st)) return 0xffffffffu;
     const int r = code == 0xffffffffu ? -1 : (hv.bits ? mask_rank(hv, q) : hv.vals[q]);
@@ -746,13 +746,19 @@ __global__ void __launch_bounds__(256) k_particle_bins(int64_t n, const uint32_t
                                                        DevStatus* st) {
     __shared__ int hist[BIN_SPAN];
     __shared__ uint32_t wmin[8], wmax[8];
-    if (cta_aborted(st)) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * BIN_PL + lane;
+    uint32_t code[BIN_PL];
+#pragma unroll
+    for (int h = 0; h < BIN_PL; ++h) {   // read before the abort test: in bounds, and it overlaps them
+        const int64_t p = p0 + 32 * h;
+        code[h] = p < n ? pcode[p] : 0xffffffffu;
+    }
+    if (cta_aborted(st)) return;
     bool miss = false;
     uint32_t k[BIN_PL];
 #pragma unroll
-    for (int h = 0; h < BIN_PL; ++h) k[h] = bin_key(p0 + 32 * h, n, pcode, hv, B3, st, miss);
+    for (int h = 0; h < BIN_PL; ++h) k[h] = bin_key(p0 + 32 * h, n, code[h], hv, B3, st, miss);
     if (miss) raise_flag(st, &st->map_miss, 1u);
     // key range of the CTA's valid keys (invalid keys are all ones)
     uint32_t lo = 0xffffffffu, hi = 0u;
@@ -1086,12 +1092,11 @@ __global__ void __launch_bounds__(256) k_scatter_kmajor(int64_t n, const uint32_
                                                         const int* __restrict__ kpre, const int* __restrict__ ccount,
                                                         uint32_t* __restrict__ skey, uint32_t* __restrict__ perm,
                                                         DevStatus* st) {
-    if (cta_aborted(st)) return;
     const int lane = threadIdx.x & 31;
     const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * SCT_PL + lane;
     uint32_t k[SCT_PL], rk[SCT_PL];
 #pragma unroll
-    for (int h = 0; h < SCT_PL; ++h) {
+    for (int h = 0; h < SCT_PL; ++h) {   // read before the abort test: in bounds, and it overlaps them
         const int64_t p = p0 + 32 * h;
         k[h] = 0xffffffffu;
         rk[h] = 0u;
@@ -1100,6 +1105,7 @@ __global__ void __launch_bounds__(256) k_scatter_kmajor(int64_t n, const uint32_
             rk[h] = prank[p];
         }
     }
+    if (cta_aborted(st)) return;
 #pragma unroll
     for (int h = 0; h < SCT_PL; ++h) {
         if (k[h] == 0xffffffffu) continue;

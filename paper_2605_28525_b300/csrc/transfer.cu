@@ -1091,11 +1091,18 @@ __global__ void __launch_bounds__(THREADS, 65536 / (THREADS * REGS)) k_g2p(const
                                               int64_t n, const int* __restrict__ nbr, Params P,
                                               const float4* __restrict__ gv, DevStatus* st) {
     constexpr int S3 = (B == 4) ? 6 : 0;
-    if (cta_aborted(st)) return;
+    // the permutation and key are read before the abort test (in bounds
+    // whatever they hold), so that their latency overlaps it; nothing they
+    // index is read before it
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t p = 0u, sk = 0u;
+    if (i < n) {
+        p = perm[i];
+        sk = skey[i];
+    }
+    if (cta_aborted(st)) return;
     if (i >= n) return;
-    const uint32_t p = perm[i];
-    const int r = (int)(skey[i] >> S3);
+    const int r = (int)(sk >> S3);
     if (!index_ok(p, n, st) || !index_ok(r, P.cap_blocks, st)) return;
     g2p_particle<B, DENSE, MAT>(ps, po, stride, p, i, r, nbr, P, gv, st);
 }
