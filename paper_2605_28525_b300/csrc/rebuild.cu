@@ -95,7 +95,9 @@ __device__ int hash_insert(const HashView& hv, uint64_t key, uint32_t rkey, int 
                            uint32_t* __restrict__ bmask, DevStatus* st, unsigned& err) {
     uint64_t s = mix64(key) & hv.mask;
     for (int r = 0; r < max_probe; ++r) {
-        unsigned long long cur = *((volatile unsigned long long*)&hv.keys[s]);
+        // an L1-cached read: a key, once claimed, stays for the whole step, so a
+        // stale copy can only read EMPTY, and the CAS below then decides
+        unsigned long long cur = __ldca(&hv.keys[s]);
         if (cur == key) return (int)s;
         if (cur == EMPTY_KEY) {
             unsigned long long old = atomicCAS(&hv.keys[s], EMPTY_KEY, (unsigned long long)key);
