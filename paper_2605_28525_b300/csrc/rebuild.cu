@@ -21,17 +21,25 @@
 //                     boxes whose mask would be too large.)
 //   k_neighbours      Phi of the blocks b + {0,1}^3 (b + {0,1,2}^3 for B = 1)
 //                     of every active block, for P2G and G2P.
-//   k_particle_keys   sort key (Phi(b(base)), l(base)) per particle, then a
-//                     radix sort (deterministic mode), and k_ranges: particle
-//                     range of every block that holds particles and the list
-//                     of such blocks.
-//   k_particle_bins   fast mode instead: a counting sort.  Bin (Phi, cell) and
-//   k_scan_tiles      rank in the bin per particle, a tile scan of the bins,
-//   k_bin_scatter     the scatter into (block, cell) order, then the particle
-//   k_block_ranges    ranges and the neighbour table in one pass.
-//   k_interleave      k-major particle order inside every block (the k-th
-//                     particle of each cell, then the next), and the particle
-//                     count per cell, for the cell-lane P2G.
+//   k_particle_keys   dense grid: sort key (Phi(b(base)), l(base)) per
+//                     particle, a radix sort, and k_ranges: particle range of
+//                     every block that holds particles and the list of such
+//                     blocks.
+//   k_particle_bins   sparse grid: a counting sort.  Bin (Phi, cell) and
+//   k_scan_tiles      rank in the bin per particle, and a tile scan of the
+//                     bins; then
+//   k_block_prep      in the fast mode at B = 4: per block, its particle
+//   k_scatter_kmajor  range, neighbour table and cells ordered by count, and
+//                     one scatter straight to the k-major order (the k-th
+//                     particle of each cell, then the next) by its closed
+//                     form;
+//   k_bin_scatter     otherwise (deterministic mode, B = 1): the scatter
+//   k_block_ranges    into (block, cell) order, then the particle ranges and
+//                     the neighbour table;
+//   k_interleave      at B = 4 after those and after the dense grid's radix
+//                     sort: the k-major order inside every block (each
+//                     cell's particles in id order in deterministic mode)
+//                     and the particle count per cell.
 #include <algorithm>
 
 #include "mpm_internal.cuh"
