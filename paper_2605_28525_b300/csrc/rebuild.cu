@@ -195,9 +195,16 @@ __device__ __forceinline__ Stencil<B> particle_stencil(const float* __restrict__
         int nbk[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) nbk[a] = ((base[a] + 2) >> S) - t.b0[a] + 1;
+        if (B == 4) {
+            // bit j = 4 ex + 2 ey + ez: the offsets allowed along each axis as
+            // masks (ex = 0 only: bits 0-3; ey = 0 only: 0, 1, 4, 5; ez = 0
+            // only: the even bits), and their intersection
+            t.need = (nbk[0] > 1 ? 0xffu : 0x0fu) & (nbk[1] > 1 ? 0xffu : 0x33u) & (nbk[2] > 1 ? 0xffu : 0x55u);
+        } else {
 #pragma unroll
-        for (int j = 0; j < NJ; ++j)
-            if (j / (R * R) < nbk[0] && (j / R) % R < nbk[1] && j % R < nbk[2]) t.need |= 1u << j;
+            for (int j = 0; j < NJ; ++j)
+                if (j / (R * R) < nbk[0] && (j / R) % R < nbk[1] && j % R < nbk[2]) t.need |= 1u << j;
+        }
     }
     // An ensemble's scenario s has its blocks ens_pitch * s further along x.
     if (P.n_scen > 1 && t.ok) t.b0[0] += scenario_of(P, __float_as_uint(ps[pel(p, PID)])) * P.ens_pitch;
