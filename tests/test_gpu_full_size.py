@@ -21,13 +21,17 @@ from tests.helpers import U32, eq_keys, oracle_for, phi_index as _phi_index, spa
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("name", ["column_collapse_1M", "landslide_8M"])
-def test_full_size_parity(oracle_mod, name):
+@pytest.mark.parametrize("name,steps", [("column_collapse_1M", 3), ("column_collapse_1M", 500), ("landslide_8M", 3),
+                                        ("landslide_8M", 300)])
+def test_full_size_parity(oracle_mod, name, steps):
+    """At the start of the run and after some hundred steps of flow, when the
+    cells' particle counts have spread (fuller cells, more rounds per P2G work
+    unit, more plastic particles)."""
     import torch
     wl = W.column_collapse() if name == "column_collapse_1M" else W.landslide()
     o = oracle_for(wl)
     sim = mpm.Simulation.from_workload(wl, stream=torch.cuda.current_stream(), device_inputs=True)
-    sim.step(3)
+    sim.step(steps)
     st = sim.read_particles()
     x, v, Cm, F = st["x"], st["v"], st["C"], st["F"]
     phi = wl.phi
