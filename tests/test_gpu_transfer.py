@@ -307,6 +307,24 @@ def test_trajectory_drucker_prager_column(oracle_mod):
     assert np.abs(out["x"] - x).max() <= 1e-4
 
 
+def test_trajectory_landslide_on_terrain(oracle_mod):
+    """A small landslide (10,240 particles, per-particle friction angles,
+    Drucker-Prager) released on the fBm terrain level set with its Coulomb
+    contact, in the slope frame with tilted gravity: 200 steps against the
+    oracle; positions within 1e-4 of the 10 m release length."""
+    wl = W.landslide(release_cells=(20, 16, 4), grid=(128, 64, 96), release_x0=10, steps=200)
+    o = oracle_for(wl)
+    sim = make_sim(wl)
+    sim.step(wl.steps)
+    out = sim.read_particles()
+    x, v, Cm, F = o.run(wl.x, None, None, None, wl.phi, nsteps=wl.steps)
+    moved = np.abs(x - wl.x.astype(np.float64)).max()
+    assert moved > 0.05   # the mass slid
+    err = np.abs(out["x"] - x).max()
+    print("max |dx| %.3g m after %d steps (largest displacement %.3g m)" % (err, wl.steps, moved))
+    assert err <= 1e-4 * 10.0
+
+
 def test_sparse_equals_dense_bitwise(oracle_mod):
     """Deterministic mode: GPU sparse and GPU dense give identical bits at every
     step (the paper's 'identical results' claim)."""
